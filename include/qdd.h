@@ -1,0 +1,258 @@
+/*
+ * qdd.h -- C ABI of libqdd, a GB300 (sm_103a) solver for the Wilson-clover
+ * Dirac equation D x = b by flexible GMRES preconditioned with the Schwarz
+ * alternating procedure (multiplicative Schwarz, "SAP") whose domain solver is
+ * minimal-residual (MR) with even-odd preconditioning, as described in
+ * arXiv:1502.04025, Sec. 3.1 ("Algorithm and implementation overview").
+ *
+ * Host layouts (every pointer argument named "host layout"):
+ *   site index   n = x + Lx*(y + Ly*(z + Lz*t))  (x fastest), periodic lattice
+ *   links        double complex U[n][mu][a][b], mu = 0..3 for x,y,z,t;
+ *                U_mu(n) joins n to n+mu.  Re/Im interleaved, 18 doubles per link.
+ *   spinors      double complex psi[n][s][c], s = 0..3 spin, c = 0..2 colour;
+ *                24 doubles per site; nrhs spinors are stored back to back.
+ * Conventions of the operator (the paper names it but prints no formula):
+ *   D = A - kappa*H,
+ *   H psi(n) = sum_mu (1-gamma_mu) U_mu(n) psi(n+mu) + (1+gamma_mu) U_mu(n-mu)^+ psi(n-mu),
+ *   A(n) = 1 + i kappa c_sw sum_{mu<nu} sigma_{mu nu} F_{mu nu}(n),
+ *   sigma_{mu nu} = (i/2)[gamma_mu, gamma_nu], F = traceless part of (Q - Q^+)/8,
+ *   Q the four-leaf clover; gammas in the Hermitian chiral basis with
+ *   gamma_5 = diag(1,1,-1,-1).
+ *
+ * Ownership: the caller owns every buffer it passes; the library owns the
+ * objects it creates (context, gauge field, their device copies) until the
+ * matching destroy call.  Pointers flagged "on_device" are CUDA device
+ * pointers of the context's device; otherwise host pointers.  "stream" is a
+ * cudaStream_t (NULL = the legacy default stream); every call returns only
+ * after its results are in the caller's buffers.
+ *
+ * Errors: every call returns a qdd_status; QDD_OK is 0.  On failure the
+ * thread-local message of qdd_last_error() says why.  No call aborts the
+ * process.  A non-converged solve returns QDD_ENOCONV with x holding the best
+ * iterate and the report filled in.
+ */
+#ifndef QDD_H
+#define QDD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qdd_ctx qdd_ctx;
+typedef struct qdd_gauge qdd_gauge;
+
+typedef enum {
+    QDD_OK = 0,
+    QDD_EINVAL = 1,   /* invalid argument (sizes, geometry, null pointer) */
+    QDD_ENOMEM = 2,   /* device or host allocation failed */
+    QDD_EBUDGET = 3,  /* the request would exceed the context's HBM budget */
+    QDD_ENOCONV = 4,  /* solver stopped at max_restarts without reaching tol */
+    QDD_ENAN = 5,     /* a NaN or Inf appeared in a residual */
+    QDD_ETIMEOUT = 6, /* a bounded wait ran out (device flag or host poll) */
+    QDD_ECUDA = 7,    /* a CUDA runtime call failed */
+    QDD_ENOTREADY = 8 /* serving: the ticket is still in flight */
+} qdd_status;
+
+/* Precision of the Schwarz preconditioner (arithmetic / storage), and of the
+ * operator inside the Arnoldi step.  The outer FGMRES vector algebra is
+ * always FP64.  F16S / BF16S: FP32 arithmetic on 16-bit storage of links
+ * (unscaled, |U_ab| <= 1), clover blocks and residual spinors (one FP32
+ * scale per site, stored values in [-1, 1]); the paper stores links and
+ * clover in half precision with single-precision spinors (Sec. 3.3). */
+typedef enum {
+    QDD_PREC_F64 = 0,
+    QDD_PREC_F32 = 1,
+    QDD_PREC_F16S = 2,
+    QDD_PREC_BF16S = 3
+} qdd_prec;
+
+typedef struct {
+    double tol;           /* stop when |b - D x| <= tol |b| (true FP64 residual) */
+    int restart_m;        /* FGMRES cycle length m (<= 64) */
+    int max_restarts;     /* restarts after the first cycle */
+    int nmr;              /* MR steps per domain visit */
+    int ncy;              /* Schwarz cycles per preconditioner application */
+    qdd_prec sap_prec;    /* preconditioner precision */
+    qdd_prec arnoldi_prec;/* QDD_PREC_F64 or QDD_PREC_F32: operator in w = D z_j */
+    int use_sap;          /* 0: no preconditioner (plain GMRES) */
+    int nrhs;             /* right-hand sides solved together (1..12) */
+    int reorth;           /* Gram-Schmidt: 0 classical, 1 classical with
+                             selective re-orthogonalisation, 2 twice always */
+} qdd_solve_params;
+
+typedef struct {
+    int converged;          /* all right-hand sides reached tol */
+    int iters;              /* Arnoldi steps (lockstep over right-hand sides) */
+    int restarts;           /* restarts performed */
+    double true_rel_res;    /* max over rhs of |b - D x| / |b| at return */
+    double est_rel_res;     /* max over rhs of the last Givens estimate */
+    double seconds;         /* host wall time of the call */
+    double ms_sap;          /* device time in the Schwarz kernels (profiling on) */
+    double ms_dslash;       /* device time in full-lattice operator kernels */
+    double ms_blas;         /* device time in FP64 vector kernels */
+    long long sap_launches; /* Schwarz block-kernel launches */
+    long long kernel_launches; /* all kernel launches of the call */
+    int n_history;          /* entries of res_history */
+    const double *res_history; /* estimated relative residual per iteration of
+                                  rhs 0, and the true one at each restart;
+                                  library-owned, valid until the next solve */
+} qdd_report;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes caps the device
+ * memory the context may hold (0 = 80% of the device's total memory);
+ * allocations beyond it fail with QDD_EBUDGET. */
+qdd_status qdd_create(qdd_ctx **ctx, int device, size_t hbm_budget_bytes);
+void qdd_destroy(qdd_ctx *ctx);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *qdd_last_error(void);
+
+/* Per-kernel-class device timing with CUDA events (adds an event pair around
+ * every timed launch).  Results land in qdd_report's ms_* fields and in
+ * qdd_get_kernel_times. */
+qdd_status qdd_set_profiling(qdd_ctx *ctx, int on);
+
+/* Kernel-class timings of the context since the last reset:
+ * out[0..1] = (ms, launches) of SAP block kernels, out[2..3] of full-lattice
+ * operator kernels, out[4..5] of FP64 vector kernels.  reset != 0 zeroes them. */
+qdd_status qdd_get_kernel_times(qdd_ctx *ctx, double out[6], int reset);
+
+/* Bytes of device memory the context holds now, and its budget. */
+qdd_status qdd_memory(qdd_ctx *ctx, size_t *used, size_t *budget);
+
+/* ------------------------------------------------------------ gauge field */
+
+/*
+ * Upload a gauge field and fix its domain decomposition (Sec. 3.1: the
+ * lattice is split into domains; Sec. 3.3: domains of 4^4 or 8x4^3 sites).
+ * L[4]: lattice extents; dom[4]: domain extents.  Each dom[mu] must be even
+ * and divide L[mu], and L[mu]/dom[mu] must be even (>= 2), so that the
+ * two-colour checkerboard of domains is consistent; the product of dom must
+ * be <= 512.  links: host layout, on the host or (links_on_device) the
+ * device.  The device keeps FP64 links in a domain-blocked, parity-split,
+ * plane-major layout, plus lower-precision copies made on demand.
+ */
+qdd_status qdd_create_gauge_field(qdd_ctx *ctx, const int L[4], const int dom[4], const double *links,
+                                  int links_on_device, qdd_gauge **g);
+void qdd_destroy_gauge(qdd_gauge *g);
+
+/*
+ * Build the clover term A = 1 + i kappa c_sw sum sigma F (two Hermitian 6x6
+ * chirality blocks per site) and the inverse blocks on odd sites used by the
+ * even-odd domain solver (Sec. 3.1, footnote on the domain inversion).  Must
+ * be called before apply_D / sap_apply / solve; may be called again with new
+ * (c_sw, kappa).  Returns QDD_EINVAL if a block is singular.
+ */
+qdd_status qdd_set_clover(qdd_gauge *g, double c_sw, double kappa);
+
+/*
+ * Clover blocks in the host site order: out[n][blk][i][j] complex (V*2*36
+ * complex), blk 0 = spins {0,1}, blk 1 = spins {2,3}, index i = s*3 + c
+ * within the block.  which = 0: A on every site; which = 1: the Schwarz form
+ * (A on even sites, A^{-1} on odd sites).  out: host pointer.
+ */
+qdd_status qdd_get_clover(qdd_gauge *g, int which, double *out);
+
+/* ------------------------------------------------------------- operators */
+
+/*
+ * out = D in for nrhs spinors (host layout), periodic boundary conditions.
+ * prec = QDD_PREC_F64 computes in FP64; QDD_PREC_F32 converts links, clover
+ * and input to FP32 and computes in FP32 (1848 flop per site); F16S / BF16S
+ * read 16-bit links/clover/spinor with FP32 arithmetic.
+ */
+qdd_status qdd_apply_D(qdd_gauge *g, const double *in, double *out, int nrhs, qdd_prec prec, int on_device,
+                       void *stream);
+
+/*
+ * One application of the Schwarz preconditioner psi = M eta (Sec. 3.1): zero
+ * start, n_half colour half-sweeps (colour 0, 1, 0, ...; 2*ncy for ncy
+ * cycles), each running nmr even-odd MR steps on every domain of the colour
+ * with Dirichlet boundaries, then updating the residual of the neighbouring
+ * domains.  rho (may be NULL) receives the maintained residual eta - D psi.
+ * eta, psi, rho: host layout, nrhs spinors each.
+ */
+qdd_status qdd_sap_apply(qdd_gauge *g, const double *eta, double *psi, double *rho, int nrhs, int nmr, int n_half,
+                         qdd_prec prec, int on_device, void *stream);
+
+/* ----------------------------------------------------------------- solver */
+
+/* Default parameters: tol 1e-10, m 16, 50 restarts, nmr 4, ncy 4, F32 SAP,
+ * F64 Arnoldi operator, SAP on, 1 rhs, selective re-orthogonalisation. */
+void qdd_default_params(qdd_solve_params *p);
+
+/*
+ * Solve D x = b (Sec. 3.1: flexible GMRES, right-preconditioned by SAP) for
+ * p->nrhs right-hand sides in host layout.  x is an output (zero initial
+ * guess).  Convergence is tested on the true FP64 residual recomputed at
+ * every restart.  rep may be NULL.
+ */
+qdd_status qdd_solve(qdd_gauge *g, const double *b, double *x, int on_device, const qdd_solve_params *p,
+                     qdd_report *rep, void *stream);
+
+/* --------------------------------------------------------- vector algebra */
+
+/*
+ * out[i] = <v_i, w> = sum_k conj(v_i[k]) w[k] for i < nvec: the fused
+ * multi-dot of the Gram-Schmidt step of FGMRES (Sec. 3.1).  v: nvec complex
+ * FP64 vectors of n elements at stride ld elements; w: n elements;
+ * out: nvec complex (device).  All device pointers; n <= 2^40, nvec <= 64.
+ * Uses library-owned device scratch for the per-block partial sums.
+ */
+qdd_status qdd_cdot_multi(qdd_ctx *ctx, const double *v, int nvec, int64_t ld, const double *w, int64_t n,
+                          double *out, void *stream);
+
+/* ------------------------------------------------------------- host logic */
+
+/* Average load of a colour half-sweep: x / ceil(x) with x = domains per
+ * colour / slots (Sec. 3.5, "Inter-core parallelization"). */
+double qdd_load_model(double n_domains_per_colour, double n_slots);
+
+/* Working set of one domain in bytes (Sec. 3.3): per site 4 links (72 reals)
+ * and 2 clover blocks (72 reals) stored with link_bytes bytes per real, plus
+ * single-precision spinors: n_full on every site (24 reals) and n_even on
+ * the even sites only (12 reals per site on average), times the domain
+ * volume. */
+double qdd_domain_working_set(const int dom[4], int link_bytes, int n_full, int n_even);
+
+/*
+ * The device layout of a lattice and domain shape (host logic only; no GPU
+ * needed), for checking: site_of[i] (V entries) is the host site index of
+ * internal index i = slot*Vd + s; nbl (Vd*8) the neighbour slot of each
+ * domain site in direction k = 2*mu + (0 forward, 1 backward), wrapped into the
+ * domain, with bit 15 set when the hop leaves the domain; nbd (Nd*8) the
+ * neighbouring domain slot.  Any output may be NULL.  Domain slots are
+ * colour-major (all domains of colour 0 first), sites parity-split.
+ */
+qdd_status qdd_layout(const int L[4], const int dom[4], int *site_of, uint16_t *nbl, int *nbd);
+
+/* ---------------------------------------------------------------- serving */
+
+/*
+ * Asynchronous solve: enqueue (g, b, x, p) and return a ticket at once.  The
+ * context's scheduler admits queued requests while the HBM budget and its
+ * stream slots allow, runs admitted requests concurrently on separate
+ * streams, and fills x (host layout, host memory that must stay valid until
+ * the ticket completes).  b is copied at submit time.
+ */
+qdd_status qdd_submit(qdd_ctx *ctx, qdd_gauge *g, const double *b, double *x, const qdd_solve_params *p,
+                      uint64_t *ticket);
+
+/* Wait up to timeout_s seconds for a ticket.  QDD_OK / the solve's status
+ * when done (rep filled, ticket retired); QDD_ENOTREADY if still running
+ * after the wait; QDD_EINVAL for an unknown ticket. */
+qdd_status qdd_poll(qdd_ctx *ctx, uint64_t ticket, qdd_report *rep, double timeout_s);
+
+/* Serving-loop settings: max concurrently running requests (stream slots). */
+qdd_status qdd_serve_config(qdd_ctx *ctx, int max_slots);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QDD_H */

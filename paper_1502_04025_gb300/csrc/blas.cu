@@ -1,0 +1,232 @@
+// FP64 complex vector algebra of the outer flexible GMRES (arXiv:1502.04025,
+// Sec. 3.1: the outer solver is flexible GMRES).  Gram-Schmidt, norms,
+// basis updates and the solution update run in FP64 on the device.
+//
+// Vectors are flat arrays of complex FP64 (double2); the lattice layout does
+// not matter here.  All reductions are two-pass and deterministic: a fixed
+// number of blocks (a multiple of the SM count) writes per-block partials in a
+// fixed order, one block sums them in a fixed order.  Fused forms read each
+// vector once: the multi-dot reads w once for all basis vectors, the
+// multi-axpy writes w once and returns its new norm.
+#include "internal.h"
+
+namespace qdd {
+
+constexpr int kBT = 256;       // threads per block
+constexpr int kNV = 16;        // basis vectors per pass
+
+int blas_blocks(const Ctx *ctx, int64_t n)
+{
+    int64_t want = (n + kBT - 1) / kBT;
+    int64_t cap = 2LL * (ctx->nsm > 0 ? ctx->nsm : 148);
+    if (want > cap) want = cap;
+    return (int)(want < 1 ? 1 : want);
+}
+
+size_t blas_scratch_elems(const Ctx *ctx) { return (size_t)2 * (ctx->nsm > 0 ? ctx->nsm : 148) * kNV; }
+
+__device__ __forceinline__ double2 dsum2(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+
+// sum of NV double2 over the block; result valid in threads 0..NV-1 via sm
+template <int NV>
+__device__ __forceinline__ void block_reduce(double2 *acc, double2 *sm /* [kBT/32][NV] */)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < NV; j++) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            acc[j].x += __shfl_xor_sync(0xffffffffu, acc[j].x, o);
+            acc[j].y += __shfl_xor_sync(0xffffffffu, acc[j].y, o);
+        }
+        if (lane == 0) sm[w * NV + j] = acc[j];
+    }
+    __syncthreads();
+}
+
+template <int NV>
+__global__ void __launch_bounds__(kBT) k_cdot_partial(const double2 *__restrict__ v, int nvec, int64_t ld,
+                                                      const double2 *__restrict__ w, int64_t n, double2 *part)
+{
+    __shared__ double2 sm[(kBT / 32) * NV];
+    double2 acc[NV];
+#pragma unroll
+    for (int j = 0; j < NV; j++) acc[j] = make_double2(0, 0);
+    for (int64_t k = (int64_t)blockIdx.x * kBT + threadIdx.x; k < n; k += (int64_t)gridDim.x * kBT) {
+        double2 b = __ldg(w + k);
+#pragma unroll
+        for (int j = 0; j < NV; j++)
+            if (j < nvec) {
+                double2 a = __ldg(v + j * ld + k);
+                acc[j].x = fma(a.x, b.x, acc[j].x);
+                acc[j].x = fma(a.y, b.y, acc[j].x);
+                acc[j].y = fma(a.x, b.y, acc[j].y);
+                acc[j].y = fma(-a.y, b.x, acc[j].y);
+            }
+    }
+    block_reduce<NV>(acc, sm);
+    if (threadIdx.x < NV) {
+        double2 s = make_double2(0, 0);
+        for (int ww = 0; ww < kBT / 32; ww++) s = dsum2(s, sm[ww * NV + threadIdx.x]);
+        part[(int64_t)blockIdx.x * NV + threadIdx.x] = s;
+    }
+}
+
+// out[j] = sum over blocks of part[b*stride + j], j < nvec; one block per j
+__global__ void __launch_bounds__(kBT) k_reduce_final(const double2 *part, int nblk, int stride, double2 *out,
+                                                      int sqrt_x)
+{
+    __shared__ double2 sm[kBT / 32];
+    const int j = blockIdx.x;
+    double2 s = make_double2(0, 0);
+    for (int b = threadIdx.x; b < nblk; b += kBT) s = dsum2(s, part[(int64_t)b * stride + j]);
+    double2 acc[1] = {s};
+    block_reduce<1>(acc, sm);
+    if (threadIdx.x == 0) {
+        double2 t = make_double2(0, 0);
+        for (int ww = 0; ww < kBT / 32; ww++) t = dsum2(t, sm[ww]);
+        out[j] = t;
+    }
+}
+
+// w -= sum_j coef[j] v_j (j < nvec); optional per-block partial of |w|^2
+template <int NV>
+__global__ void __launch_bounds__(kBT) k_caxpy_norm(const double2 *__restrict__ v, int nvec, int64_t ld,
+                                                    const double2 *__restrict__ coef, double2 *w, int64_t n,
+                                                    double2 *part)
+{
+    __shared__ double2 sm[kBT / 32];
+    double2 c[NV];
+#pragma unroll
+    for (int j = 0; j < NV; j++) c[j] = j < nvec ? coef[j] : make_double2(0, 0);
+    double nrm = 0;
+    for (int64_t k = (int64_t)blockIdx.x * kBT + threadIdx.x; k < n; k += (int64_t)gridDim.x * kBT) {
+        double2 b = w[k];
+#pragma unroll
+        for (int j = 0; j < NV; j++)
+            if (j < nvec) {
+                double2 a = __ldg(v + j * ld + k);
+                b.x = fma(-c[j].x, a.x, b.x);
+                b.x = fma(c[j].y, a.y, b.x);
+                b.y = fma(-c[j].x, a.y, b.y);
+                b.y = fma(-c[j].y, a.x, b.y);
+            }
+        if (nvec > 0) w[k] = b;
+        nrm = fma(b.x, b.x, nrm);
+        nrm = fma(b.y, b.y, nrm);
+    }
+    if (part) {
+        double2 acc[1] = {make_double2(nrm, 0)};
+        block_reduce<1>(acc, sm);
+        if (threadIdx.x == 0) {
+            double2 t = make_double2(0, 0);
+            for (int ww = 0; ww < kBT / 32; ww++) t = dsum2(t, sm[ww]);
+            part[blockIdx.x] = t;
+        }
+    }
+}
+
+// out = w / sqrt(norm2[0]) (out may alias w)
+__global__ void k_scale_by_norm(const double2 *w, int64_t n, const double2 *norm2, double2 *out)
+{
+    double nn = norm2[0].x;
+    double f = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
+    for (int64_t k = (int64_t)blockIdx.x * kBT + threadIdx.x; k < n; k += (int64_t)gridDim.x * kBT) {
+        double2 a = w[k];
+        out[k] = make_double2(a.x * f, a.y * f);
+    }
+}
+
+// x += sum_j coef[j] z_j, z in FP64 or FP32
+template <typename T2>
+__global__ void __launch_bounds__(kBT) k_axpy_multi(const T2 *__restrict__ z, int nvec, int64_t ld,
+                                                    const double2 *__restrict__ coef, double2 *x, int64_t n)
+{
+    for (int64_t k = (int64_t)blockIdx.x * kBT + threadIdx.x; k < n; k += (int64_t)gridDim.x * kBT) {
+        double2 b = x[k];
+        for (int j = 0; j < nvec; j++) {
+            T2 a = z[j * ld + k];
+            double2 cj = coef[j];
+            double ax = (double)a.x, ay = (double)a.y;
+            b.x = fma(cj.x, ax, b.x);
+            b.x = fma(-cj.y, ay, b.x);
+            b.y = fma(cj.x, ay, b.y);
+            b.y = fma(cj.y, ax, b.y);
+        }
+        x[k] = b;
+    }
+}
+
+// ------------------------------------------------------------- launchers
+
+qdd_status blas_cdot_multi(Ctx *ctx, const double2 *v, int nvec, int64_t ld, const double2 *w, int64_t n,
+                           double2 *out, double2 *scratch, cudaStream_t s)
+{
+    if (nvec <= 0) return QDD_OK;
+    const int nb = blas_blocks(ctx, n);
+    for (int j0 = 0; j0 < nvec; j0 += kNV) {
+        int nv = nvec - j0 < kNV ? nvec - j0 : kNV;
+        {
+            LaunchScope ls(ctx->timer, K_BLAS, s);
+            k_cdot_partial<kNV><<<nb, kBT, 0, s>>>(v + j0 * ld, nv, ld, w, n, scratch);
+        }
+        {
+            LaunchScope ls(ctx->timer, K_BLAS, s);
+            k_reduce_final<<<nv, kBT, 0, s>>>(scratch, nb, kNV, out + j0, 0);
+        }
+    }
+    QDD_CUDA(cudaGetLastError());
+    return QDD_OK;
+}
+
+qdd_status blas_caxpy_multi_norm(Ctx *ctx, const double2 *v, int nvec, int64_t ld, const double2 *coef, double2 *w,
+                                 int64_t n, double2 *norm2_out, double2 *scratch, cudaStream_t s)
+{
+    const int nb = blas_blocks(ctx, n);
+    int j0 = 0;
+    do {
+        int nv = nvec - j0 < kNV ? nvec - j0 : kNV;
+        bool last = j0 + nv >= nvec;
+        {
+            LaunchScope ls(ctx->timer, K_BLAS, s);
+            k_caxpy_norm<kNV><<<nb, kBT, 0, s>>>(v + j0 * ld, nv, ld, coef + j0, w, n,
+                                                  (last && norm2_out) ? scratch : nullptr);
+        }
+        j0 += nv;
+    } while (j0 < nvec);
+    if (norm2_out) {
+        LaunchScope ls(ctx->timer, K_BLAS, s);
+        k_reduce_final<<<1, kBT, 0, s>>>(scratch, nb, 1, norm2_out, 0);
+    }
+    QDD_CUDA(cudaGetLastError());
+    return QDD_OK;
+}
+
+qdd_status blas_norm2(Ctx *ctx, const double2 *w, int64_t n, double2 *out, double2 *scratch, cudaStream_t s)
+{
+    return blas_caxpy_multi_norm(ctx, nullptr, 0, 0, nullptr, (double2 *)w, n, out, scratch, s);
+}
+
+qdd_status blas_scale_by_norm(Ctx *ctx, const double2 *w, int64_t n, const double2 *norm2, double2 *out,
+                              cudaStream_t s)
+{
+    LaunchScope ls(ctx->timer, K_BLAS, s);
+    k_scale_by_norm<<<blas_blocks(ctx, n), kBT, 0, s>>>(w, n, norm2, out);
+    QDD_CUDA(cudaGetLastError());
+    return QDD_OK;
+}
+
+qdd_status blas_axpy_multi(Ctx *ctx, const void *z, bool z_f32, int nvec, int64_t ld, const double2 *coef,
+                           double2 *x, int64_t n, cudaStream_t s)
+{
+    if (nvec <= 0) return QDD_OK;
+    LaunchScope ls(ctx->timer, K_BLAS, s);
+    if (z_f32)
+        k_axpy_multi<float2><<<blas_blocks(ctx, n), kBT, 0, s>>>((const float2 *)z, nvec, ld, coef, x, n);
+    else
+        k_axpy_multi<double2><<<blas_blocks(ctx, n), kBT, 0, s>>>((const double2 *)z, nvec, ld, coef, x, n);
+    QDD_CUDA(cudaGetLastError());
+    return QDD_OK;
+}
+
+}  // namespace qdd

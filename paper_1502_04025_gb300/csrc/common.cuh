@@ -1,0 +1,292 @@
+// Shared device-side definitions of libqdd: complex arithmetic, storage
+// precisions, the domain-blocked field layout and the spin algebra of the
+// Wilson-clover operator (arXiv:1502.04025, Sec. 3.1-3.2).
+//
+// Device layout of every lattice field (Sec. 3.2 chooses a layout for the
+// domain-decomposed algorithm; this one is chosen for coalesced GPU access
+// and for one contiguous block per domain, so a domain stages with a single
+// bulk copy):
+//   domain slot d  : colour-major, d = colour*(Nd/2) + (block index >> 1)
+//   site slot s    : parity-split within the domain, s = parity*(Vd/2) + (l >> 1),
+//                    l the domain-local lexicographic index
+//   element        : plane-major per domain, field[(d*planes + p)*Vd + s],
+//                    one complex number per plane entry
+// Planes: spinor 12 (p = spin*3 + colour); links 36 (p = mu*9 + a*3 + b);
+// clover 36 (18 per chirality block: 3 pairs of real diagonal entries, then
+// the 15 upper off-diagonal entries row by row).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace qdd {
+
+// ------------------------------------------------------------------ complex
+
+template <typename R>
+struct cpx {
+    R re, im;
+};
+
+template <typename R>
+__host__ __device__ __forceinline__ cpx<R> mk(R a, R b) { return cpx<R>{a, b}; }
+template <typename R>
+__device__ __forceinline__ cpx<R> operator+(cpx<R> a, cpx<R> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename R>
+__device__ __forceinline__ cpx<R> operator-(cpx<R> a, cpx<R> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename R>
+__device__ __forceinline__ cpx<R> operator-(cpx<R> a) { return {-a.re, -a.im}; }
+template <typename R>
+__device__ __forceinline__ cpx<R> operator*(cpx<R> a, cpx<R> b)
+{
+    return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename R>
+__device__ __forceinline__ cpx<R> operator*(R s, cpx<R> a) { return {s * a.re, s * a.im}; }
+template <typename R>
+__device__ __forceinline__ cpx<R> conj(cpx<R> a) { return {a.re, -a.im}; }
+// conj(a) * b
+template <typename R>
+__device__ __forceinline__ cpx<R> cmulc(cpx<R> a, cpx<R> b)
+{
+    return {a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re};
+}
+// i * a and -i * a
+template <typename R>
+__device__ __forceinline__ cpx<R> ti(cpx<R> a) { return {-a.im, a.re}; }
+template <typename R>
+__device__ __forceinline__ cpx<R> tmi(cpx<R> a) { return {a.im, -a.re}; }
+// acc += a * b
+template <typename R>
+__device__ __forceinline__ void cfma(cpx<R> &acc, cpx<R> a, cpx<R> b)
+{
+    acc.re = fma(a.re, b.re, acc.re);
+    acc.re = fma(-a.im, b.im, acc.re);
+    acc.im = fma(a.re, b.im, acc.im);
+    acc.im = fma(a.im, b.re, acc.im);
+}
+// acc += conj(a) * b
+template <typename R>
+__device__ __forceinline__ void cfmac(cpx<R> &acc, cpx<R> a, cpx<R> b)
+{
+    acc.re = fma(a.re, b.re, acc.re);
+    acc.re = fma(a.im, b.im, acc.re);
+    acc.im = fma(a.re, b.im, acc.im);
+    acc.im = fma(-a.im, b.re, acc.im);
+}
+
+// --------------------------------------------------------- storage formats
+
+// One complex number per plane entry.  16-bit formats of spinors and clover
+// carry one FP32 scale per site (stored value = value / scale); links are
+// stored unscaled (unitary, |U_ab| <= 1).
+struct StF64 {
+    using T2 = double2;
+    static constexpr bool kScaled = false;
+    static constexpr int kBytes = 16;
+};
+struct StF32 {
+    using T2 = float2;
+    static constexpr bool kScaled = false;
+    static constexpr int kBytes = 8;
+};
+struct StF16 {
+    using T2 = __half2;
+    static constexpr bool kScaled = true;
+    static constexpr int kBytes = 4;
+};
+struct StBF16 {
+    using T2 = __nv_bfloat162;
+    static constexpr bool kScaled = true;
+    static constexpr int kBytes = 4;
+};
+
+template <typename R>
+__device__ __forceinline__ cpx<R> ld_c(const double2 *p) { double2 v = __ldg(p); return {(R)v.x, (R)v.y}; }
+template <typename R>
+__device__ __forceinline__ cpx<R> ld_c(const float2 *p) { float2 v = __ldg(p); return {(R)v.x, (R)v.y}; }
+template <typename R>
+__device__ __forceinline__ cpx<R> ld_c(const __half2 *p)
+{
+    float2 v = __half22float2(__ldg(p));
+    return {(R)v.x, (R)v.y};
+}
+template <typename R>
+__device__ __forceinline__ cpx<R> ld_c(const __nv_bfloat162 *p)
+{
+    float2 v = __bfloat1622float2(__ldg(p));
+    return {(R)v.x, (R)v.y};
+}
+
+// plain (coherent) loads, for shared memory or buffers written in the same kernel
+template <typename R>
+__device__ __forceinline__ cpx<R> ld_s(const double2 *p) { double2 v = *p; return {(R)v.x, (R)v.y}; }
+template <typename R>
+__device__ __forceinline__ cpx<R> ld_s(const float2 *p) { float2 v = *p; return {(R)v.x, (R)v.y}; }
+template <typename R>
+__device__ __forceinline__ cpx<R> ld_s(const __half2 *p) { float2 v = __half22float2(*p); return {(R)v.x, (R)v.y}; }
+template <typename R>
+__device__ __forceinline__ cpx<R> ld_s(const __nv_bfloat162 *p)
+{
+    float2 v = __bfloat1622float2(*p);
+    return {(R)v.x, (R)v.y};
+}
+
+template <typename R>
+__device__ __forceinline__ void st_c(double2 *p, cpx<R> v) { *p = make_double2((double)v.re, (double)v.im); }
+template <typename R>
+__device__ __forceinline__ void st_c(float2 *p, cpx<R> v) { *p = make_float2((float)v.re, (float)v.im); }
+template <typename R>
+__device__ __forceinline__ void st_c(__half2 *p, cpx<R> v) { *p = __floats2half2_rn((float)v.re, (float)v.im); }
+template <typename R>
+__device__ __forceinline__ void st_c(__nv_bfloat162 *p, cpx<R> v)
+{
+    *p = __floats2bfloat162_rn((float)v.re, (float)v.im);
+}
+
+// A field in device memory: planes of Vd complex per domain, optional scale.
+template <typename S>
+struct Field {
+    typename S::T2 *p;
+    float *scale;  // [Nd*Vd], only for S::kScaled
+};
+
+// ------------------------------------------------------------------ geometry
+
+// Direction k = 2*mu + b: b = 0 the forward neighbour n+mu, b = 1 the backward n-mu.
+struct Geom {
+    int L[4], dom[4], nb[4];
+    int V, Vd, Vh, Nd, Nd2;
+    int vd_shift;          // log2(Vd) when Vd is a power of two, else -1
+    const uint16_t *nbl;   // [Vd][8]: neighbour site slot (wrapped into the domain), bit 15 = leaves the domain
+    const int *nbd;        // [Nd][8]: neighbour domain slot
+};
+
+constexpr uint16_t kCross = 0x8000;
+constexpr uint16_t kSlotMask = 0x7fff;
+
+__device__ __forceinline__ void split_index(const Geom &g, int gi, int &d, int &s)
+{
+    if (g.vd_shift >= 0) {
+        d = gi >> g.vd_shift;
+        s = gi & (g.Vd - 1);
+    } else {
+        d = gi / g.Vd;
+        s = gi - d * g.Vd;
+    }
+}
+
+// global index of the neighbour of (d, s) in direction k
+__device__ __forceinline__ int neighbour(const Geom &g, int d, int s, int k)
+{
+    uint16_t e = __ldg(g.nbl + s * 8 + k);
+    int nd = (e & kCross) ? __ldg(g.nbd + d * 8 + k) : d;
+    return nd * g.Vd + (e & kSlotMask);
+}
+
+// plane-major address: global index gi = d*Vd + s, plane p of P
+__device__ __forceinline__ int64_t paddr(const Geom &g, int gi, int p, int P)
+{
+    int d, s;
+    split_index(g, gi, d, s);
+    return ((int64_t)d * P + p) * g.Vd + s;
+}
+
+// ------------------------------------------------------------ spin algebra
+
+// Spinor component index: spin*3 + colour.  In the chiral basis
+//   gamma_mu = [[0, a_mu], [a_mu^+, 0]] (2x2 spin blocks),
+//   a_x = -i sigma_x, a_y = -i sigma_y, a_z = -i sigma_z, a_t = 1.
+// (1 - sgn*gamma_mu) psi = (h ; -sgn * a^+ h) with h = u - sgn * a l, where
+// u = spins (0,1) and l = spins (2,3) of psi.  The hopping term only needs the
+// two-spin vector h per colour (the rank-2 projection), so each hop costs two
+// SU(3) products.
+
+// h = u - sgn * (a_mu l): half spinor from a full spinor, per colour c
+template <int MU, int SGN, typename R>
+__device__ __forceinline__ void project(const cpx<R> *x, cpx<R> *h)
+{
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        cpx<R> u0 = x[0 * 3 + c], u1 = x[1 * 3 + c], l0 = x[2 * 3 + c], l1 = x[3 * 3 + c];
+        cpx<R> al0, al1;
+        if (MU == 0) { al0 = tmi(l1); al1 = tmi(l0); }       // -i sigma_x l
+        else if (MU == 1) { al0 = -l1; al1 = l0; }           // -i sigma_y l
+        else if (MU == 2) { al0 = tmi(l0); al1 = ti(l1); }   // -i sigma_z l
+        else { al0 = l0; al1 = l1; }                         // 1 l
+        if (SGN > 0) { h[c] = u0 - al0; h[3 + c] = u1 - al1; }
+        else { h[c] = u0 + al0; h[3 + c] = u1 + al1; }
+    }
+}
+
+// acc += (w ; -sgn * a_mu^+ w), w the half spinor after the colour product
+template <int MU, int SGN, typename R>
+__device__ __forceinline__ void reconstruct_add(const cpx<R> *w, cpx<R> *acc)
+{
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        cpx<R> w0 = w[c], w1 = w[3 + c];
+        cpx<R> b0, b1;  // a^+ w
+        if (MU == 0) { b0 = ti(w1); b1 = ti(w0); }          // i sigma_x w
+        else if (MU == 1) { b0 = w1; b1 = -w0; }            // i sigma_y w
+        else if (MU == 2) { b0 = ti(w0); b1 = tmi(w1); }    // i sigma_z w
+        else { b0 = w0; b1 = w1; }
+        acc[0 * 3 + c] = acc[0 * 3 + c] + w0;
+        acc[1 * 3 + c] = acc[1 * 3 + c] + w1;
+        if (SGN > 0) { acc[2 * 3 + c] = acc[2 * 3 + c] - b0; acc[3 * 3 + c] = acc[3 * 3 + c] - b1; }
+        else { acc[2 * 3 + c] = acc[2 * 3 + c] + b0; acc[3 * 3 + c] = acc[3 * 3 + c] + b1; }
+    }
+}
+
+// w = U h (DAG = false) or U^+ h (DAG = true) for the two spins of h
+template <bool DAG, typename R>
+__device__ __forceinline__ void su3_mul_half(const cpx<R> *U, const cpx<R> *h, cpx<R> *w)
+{
+#pragma unroll
+    for (int sp = 0; sp < 2; sp++)
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            cpx<R> acc = mk<R>(0, 0);
+#pragma unroll
+            for (int b = 0; b < 3; b++) {
+                if (DAG) cfmac(acc, U[b * 3 + a], h[sp * 3 + b]);
+                else cfma(acc, U[a * 3 + b], h[sp * 3 + b]);
+            }
+            w[sp * 3 + a] = acc;
+        }
+}
+
+// one hop: acc += (1 - sgn gamma_mu) V x, V = U (forward) or U^+ (backward)
+template <int MU, int SGN, typename R>
+__device__ __forceinline__ void hop(const cpx<R> *U, const cpx<R> *x, cpx<R> *acc)
+{
+    cpx<R> h[6], w[6];
+    project<MU, SGN>(x, h);
+    su3_mul_half<(SGN < 0)>(U, h, w);
+    reconstruct_add<MU, SGN>(w, acc);
+}
+
+// Hermitian 6x6 block from its packed 18 complex slots
+template <typename R>
+__device__ __forceinline__ void herm6_mul(const cpx<R> *blk, const cpx<R> *in, cpx<R> *out)
+{
+    R d[6] = {blk[0].re, blk[0].im, blk[1].re, blk[1].im, blk[2].re, blk[2].im};
+#pragma unroll
+    for (int i = 0; i < 6; i++) out[i] = d[i] * in[i];
+    int k = 3;
+#pragma unroll
+    for (int i = 0; i < 6; i++)
+#pragma unroll
+        for (int j = i + 1; j < 6; j++) {
+            cfma(out[i], blk[k], in[j]);
+            cfmac(out[j], blk[k], in[i]);
+            k++;
+        }
+}
+
+// Runtime-checked device error flags (bounded waits that ran out, etc.).
+constexpr int kErrMbarTimeout = 1;
+
+}  // namespace qdd

@@ -1,0 +1,198 @@
+// Full-lattice Wilson-clover operator  y = D x = A x - kappa H x
+// (arXiv:1502.04025, Sec. 3.1 names the operator; Sec. 3.6 counts 1848 flop
+// per site: 1320 for the eight spin-projected hops, 504 for the two Hermitian
+// 6x6 clover blocks, 24 for the final combination).
+//
+// One thread per site over the domain-blocked, plane-major layout: a warp
+// reads 32 consecutive sites of one plane (256 or 512 contiguous bytes) for
+// every link, clover and spinor component.  Neighbour sites come from a
+// per-domain-shape table (the neighbour's slot inside its domain and whether
+// the hop leaves the domain) and a per-domain table of neighbouring domains.
+// The roofline of this kernel is HBM bandwidth: each link, clover entry and
+// input spinor is read once and the output written once when the neighbour
+// re-reads hit in L1/L2.
+#include "internal.h"
+
+namespace qdd {
+
+template <typename R, typename S>
+__device__ __forceinline__ void load_spinor(const Field<S> &f, int64_t gi_plane_base, int64_t sidx, int Vd,
+                                            cpx<R> *x)
+{
+    const typename S::T2 *p = f.p + gi_plane_base;
+    R sc = S::kScaled ? (R)__ldg(f.scale + sidx) : (R)1;
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+        cpx<R> v = ld_c<R>(p + (int64_t)k * Vd);
+        x[k] = S::kScaled ? sc * v : v;
+    }
+}
+
+template <typename R, typename S>
+__device__ __forceinline__ void load_link(const Field<S> &U, int d, int s, int mu, int Vd, cpx<R> *u)
+{
+    const typename S::T2 *p = U.p + ((int64_t)d * 36 + mu * 9) * Vd + s;
+#pragma unroll
+    for (int k = 0; k < 9; k++) u[k] = ld_c<R>(p + (int64_t)k * Vd);
+}
+
+template <int MU, typename R, typename SL, typename SI>
+__device__ __forceinline__ void dslash_dir(const Geom &g, const Field<SL> &U, const Field<SI> &in, int64_t rbase,
+                                           int64_t sbase, int d, int s, cpx<R> *acc)
+{
+    cpx<R> u[9], x[12];
+    {
+        uint16_t e = __ldg(g.nbl + s * 8 + 2 * MU);
+        int nd = (e & kCross) ? __ldg(g.nbd + d * 8 + 2 * MU) : d;
+        int ns = e & kSlotMask;
+        load_spinor<R, SI>(in, rbase + (int64_t)nd * 12 * g.Vd + ns, sbase + (int64_t)nd * g.Vd + ns, g.Vd, x);
+        load_link<R, SL>(U, d, s, MU, g.Vd, u);
+        hop<MU, +1>(u, x, acc);
+    }
+    {
+        uint16_t e = __ldg(g.nbl + s * 8 + 2 * MU + 1);
+        int nd = (e & kCross) ? __ldg(g.nbd + d * 8 + 2 * MU + 1) : d;
+        int ns = e & kSlotMask;
+        load_spinor<R, SI>(in, rbase + (int64_t)nd * 12 * g.Vd + ns, sbase + (int64_t)nd * g.Vd + ns, g.Vd, x);
+        load_link<R, SL>(U, nd, ns, MU, g.Vd, u);
+        hop<MU, -1>(u, x, acc);
+    }
+}
+
+template <typename R, typename SL, typename SC, typename SI, typename SO, bool RESID>
+__global__ void __launch_bounds__(128) k_dslash(Geom g, Field<SL> U, Field<SC> A, Field<SI> in, Field<SO> out,
+                                                const double2 *b, R kappa)
+{
+    int gi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi >= g.V) return;
+    const int64_t r = blockIdx.y;
+    const int64_t rbase = r * (int64_t)g.V * 12, sbase = r * (int64_t)g.V;
+    int d, s;
+    split_index(g, gi, d, s);
+    cpx<R> acc[12];
+#pragma unroll
+    for (int k = 0; k < 12; k++) acc[k] = mk<R>(0, 0);
+    dslash_dir<0, R, SL, SI>(g, U, in, rbase, sbase, d, s, acc);
+    dslash_dir<1, R, SL, SI>(g, U, in, rbase, sbase, d, s, acc);
+    dslash_dir<2, R, SL, SI>(g, U, in, rbase, sbase, d, s, acc);
+    dslash_dir<3, R, SL, SI>(g, U, in, rbase, sbase, d, s, acc);
+
+    cpx<R> x[12];
+    load_spinor<R, SI>(in, rbase + (int64_t)d * 12 * g.Vd + s, sbase + gi, g.Vd, x);
+    cpx<R> y[12];
+    {
+        const typename SC::T2 *p = A.p + (int64_t)d * 36 * g.Vd + s;
+        R sc = SC::kScaled ? (R)__ldg(A.scale + gi) : (R)1;
+#pragma unroll
+        for (int blk = 0; blk < 2; blk++) {
+            cpx<R> m[18];
+#pragma unroll
+            for (int k = 0; k < 18; k++) {
+                cpx<R> v = ld_c<R>(p + (int64_t)(blk * 18 + k) * g.Vd);
+                m[k] = SC::kScaled ? sc * v : v;
+            }
+            herm6_mul(m, x + 6 * blk, y + 6 * blk);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+        y[k].re = fma(-kappa, acc[k].re, y[k].re);
+        y[k].im = fma(-kappa, acc[k].im, y[k].im);
+    }
+    if (RESID) {
+        const double2 *bp = b + rbase + (int64_t)d * 12 * g.Vd + s;
+#pragma unroll
+        for (int k = 0; k < 12; k++) {
+            double2 v = __ldg(bp + (int64_t)k * g.Vd);
+            y[k] = mk<R>((R)v.x - y[k].re, (R)v.y - y[k].im);
+        }
+    }
+    typename SO::T2 *op = out.p + rbase + (int64_t)d * 12 * g.Vd + s;
+    if (SO::kScaled) {
+        R m = 0;
+#pragma unroll
+        for (int k = 0; k < 12; k++) m = fmax(m, fmax(fabs(y[k].re), fabs(y[k].im)));
+        float scf = (float)m;
+        out.scale[sbase + gi] = scf;
+        R inv = m > 0 ? (R)1 / (R)scf : (R)0;
+#pragma unroll
+        for (int k = 0; k < 12; k++) st_c<R>(op + (int64_t)k * g.Vd, inv * y[k]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 12; k++) st_c<R>(op + (int64_t)k * g.Vd, y[k]);
+    }
+}
+
+template <typename R, typename SL, typename SC, typename SI, typename SO, bool RESID>
+static qdd_status run_dslash(Gauge *g, Field<SL> U, Field<SC> A, const void *in, const float *in_s, void *out,
+                             float *out_s, const double2 *b, int nrhs, cudaStream_t s)
+{
+    Field<SI> fi{(typename SI::T2 *)in, (float *)in_s};
+    Field<SO> fo{(typename SO::T2 *)out, out_s};
+    dim3 grid((g->hg.V + 127) / 128, nrhs);
+    LaunchScope ls(g->ctx->timer, K_DSLASH, s);
+    k_dslash<R, SL, SC, SI, SO, RESID><<<grid, 128, 0, s>>>(g->geom, U, A, fi, fo, b, (R)g->kappa);
+    QDD_CUDA(cudaGetLastError());
+    return QDD_OK;
+}
+
+qdd_status launch_dslash(Gauge *g, qdd_prec arith, qdd_prec fp, const void *in, const float *in_s, qdd_prec ip,
+                         void *out, float *out_s, qdd_prec op, const double2 *b, int nrhs, cudaStream_t s)
+{
+    if (!g->have_clover) {
+        set_error("set_clover has not been called");
+        return QDD_EINVAL;
+    }
+    if (arith == QDD_PREC_F64) {
+        if (fp != QDD_PREC_F64 || op != QDD_PREC_F64) {
+            set_error("FP64 operator needs FP64 fields and output");
+            return QDD_EINVAL;
+        }
+        Field<StF64> U{g->links64.as<double2>(), nullptr}, A{g->clov64.as<double2>(), nullptr};
+        switch (ip) {
+        case QDD_PREC_F64:
+            return b ? run_dslash<double, StF64, StF64, StF64, StF64, true>(g, U, A, in, in_s, out, out_s, b, nrhs, s)
+                     : run_dslash<double, StF64, StF64, StF64, StF64, false>(g, U, A, in, in_s, out, out_s, b, nrhs,
+                                                                             s);
+        case QDD_PREC_F32:
+            return run_dslash<double, StF64, StF64, StF32, StF64, false>(g, U, A, in, in_s, out, out_s, b, nrhs, s);
+        default: break;
+        }
+    } else if (arith == QDD_PREC_F32 && !b) {
+        QDD_TRY(ensure_copy(g, fp, s));
+        PrecCopy &c = g->copies[fp];
+        switch (fp) {
+        case QDD_PREC_F32: {
+            Field<StF32> U{c.links.as<float2>(), nullptr}, A{c.clov.as<float2>(), nullptr};
+            if (ip == QDD_PREC_F32 && op == QDD_PREC_F32)
+                return run_dslash<float, StF32, StF32, StF32, StF32, false>(g, U, A, in, in_s, out, out_s, b, nrhs,
+                                                                            s);
+            if (ip == QDD_PREC_F32 && op == QDD_PREC_F64)
+                return run_dslash<float, StF32, StF32, StF32, StF64, false>(g, U, A, in, in_s, out, out_s, b, nrhs,
+                                                                            s);
+            break;
+        }
+        case QDD_PREC_F16S: {
+            Field<StF16> U{c.links.as<__half2>(), nullptr}, A{c.clov.as<__half2>(), c.clov_s.as<float>()};
+            if (ip == QDD_PREC_F16S && op == QDD_PREC_F16S)
+                return run_dslash<float, StF16, StF16, StF16, StF16, false>(g, U, A, in, in_s, out, out_s, b, nrhs,
+                                                                            s);
+            break;
+        }
+        case QDD_PREC_BF16S: {
+            Field<StBF16> U{c.links.as<__nv_bfloat162>(), nullptr},
+                A{c.clov.as<__nv_bfloat162>(), c.clov_s.as<float>()};
+            if (ip == QDD_PREC_BF16S && op == QDD_PREC_BF16S)
+                return run_dslash<float, StBF16, StBF16, StBF16, StBF16, false>(g, U, A, in, in_s, out, out_s, b,
+                                                                                nrhs, s);
+            break;
+        }
+        default: break;
+        }
+    }
+    set_error("unsupported operator precision combination (arith %d, fields %d, in %d, out %d)", (int)arith, (int)fp,
+              (int)ip, (int)op);
+    return QDD_EINVAL;
+}
+
+}  // namespace qdd

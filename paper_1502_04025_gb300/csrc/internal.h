@@ -1,0 +1,245 @@
+// Host-side internals of libqdd shared by its translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <complex>
+#include <condition_variable>
+#include <cstdint>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/qdd.h"
+#include "common.cuh"
+
+namespace qdd {
+
+// ------------------------------------------------------------------ errors
+
+void set_error(const char *fmt, ...);
+void clear_error();
+
+#define QDD_CUDA(call)                                                                       \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess) {                                                             \
+            ::qdd::set_error("%s:%d: %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_)); \
+            return QDD_ECUDA;                                                                \
+        }                                                                                    \
+    } while (0)
+
+#define QDD_TRY(expr)                   \
+    do {                                \
+        qdd_status s_ = (expr);         \
+        if (s_ != QDD_OK) return s_;    \
+    } while (0)
+
+// ------------------------------------------------------------ kernel timing
+
+enum KClass { K_SAP = 0, K_DSLASH = 1, K_BLAS = 2, K_OTHER = 3 };
+
+// Launch bookkeeping of a context: launch counts always, CUDA-event timing of
+// each launch when profiling is on (events resolved at sync points).
+struct Timer {
+    bool on = false;
+    long long launches[4] = {0, 0, 0, 0};
+    double ms[4] = {0, 0, 0, 0};
+    long long timed[4] = {0, 0, 0, 0};
+    struct Pending {
+        cudaEvent_t a, b;
+        int cls;
+    };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> pool;
+    std::mutex mu;
+
+    cudaEvent_t get_event();
+    void begin(int cls, cudaStream_t s, cudaEvent_t *a);
+    void end(int cls, cudaStream_t s, cudaEvent_t a);
+    void resolve();  // after the stream has been synchronised
+    ~Timer();
+};
+
+struct LaunchScope {
+    Timer &t;
+    int cls;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr;
+    LaunchScope(Timer &t_, int cls_, cudaStream_t s_) : t(t_), cls(cls_), s(s_) { t.begin(cls, s, &a); }
+    ~LaunchScope() { t.end(cls, s, a); }
+};
+
+// ------------------------------------------------------------------- memory
+
+struct Ctx;
+
+struct DevMem {
+    Ctx *ctx = nullptr;
+    void *p = nullptr;
+    size_t bytes = 0;
+    DevMem() = default;
+    DevMem(const DevMem &) = delete;
+    DevMem &operator=(const DevMem &) = delete;
+    ~DevMem() { release(); }
+    qdd_status alloc(Ctx *c, size_t n);
+    qdd_status ensure(Ctx *c, size_t n) { return (bytes >= n && p) ? QDD_OK : alloc(c, n); }
+    void release();
+    template <typename T>
+    T *as() const { return (T *)p; }
+};
+
+// ------------------------------------------------------------------ context
+
+struct Request;
+
+struct Ctx {
+    int device = 0;
+    int nsm = 0;
+    size_t budget = 0;
+    std::atomic<size_t> used{0};
+    Timer timer;
+    // scratch of the reductions (per-block partials), grown on demand
+    DevMem red_scratch;
+    std::mutex red_mu;
+    // serving
+    std::mutex q_mu;
+    std::condition_variable q_cv, done_cv;
+    std::deque<std::shared_ptr<Request>> queue;
+    std::map<uint64_t, std::shared_ptr<Request>> tickets;
+    std::vector<std::thread> workers;
+    int max_slots = 4;
+    int running = 0;
+    uint64_t next_ticket = 1;
+    bool stopping = false;
+    ~Ctx();
+};
+
+// ------------------------------------------------------------------ geometry
+
+struct HostGeom {
+    int L[4], dom[4], nb[4];
+    int V, Vd, Vh, Nd, Nd2;
+    std::vector<int> slot_block;   // slot -> block index
+    std::vector<int> site_of;      // internal index -> host site index
+    std::vector<uint16_t> nbl;     // [Vd][8]
+    std::vector<int> nbd;          // [Nd][8]
+};
+
+qdd_status make_geometry(const int L[4], const int dom[4], HostGeom &hg);
+
+// A lower-precision copy of the fields the operator and the preconditioner read.
+struct PrecCopy {
+    bool valid = false;
+    DevMem links, clov, clov_s, sclov, sclov_s;
+};
+
+// Device and pinned host buffers of one solve (Krylov basis, preconditioner
+// fields, scalars); reused across solves and grown on demand.
+struct Workspace {
+    int nrhs = 0, m = 0;
+    qdd_prec sp = QDD_PREC_F32;
+    DevMem io, b, x, V, Z, rho, rho_s, delta, delta_s, dev, scratch, err;
+    double2 *host = nullptr;  // pinned mirror of `dev`
+    size_t host_elems = 0;
+    std::vector<double> hist;
+    ~Workspace()
+    {
+        if (host) cudaFreeHost(host);
+    }
+};
+
+struct Gauge {
+    Ctx *ctx = nullptr;
+    HostGeom hg;
+    Geom geom{};
+    DevMem d_nbl, d_nbd, d_site_of;
+    DevMem links64;           // FP64 links, internal layout
+    bool have_clover = false;
+    double csw = 0, kappa = 0;
+    DevMem clov64, sclov64;   // FP64 clover A and Schwarz form (A even, A^-1 odd)
+    PrecCopy copies[4];       // index = qdd_prec; F64 entry aliases the masters
+    std::unique_ptr<Workspace> ws;  // workspace of the synchronous entry points
+    std::mutex mu;            // one synchronous call at a time per gauge object
+    std::mutex copy_mu;       // guards the lazily built precision copies
+    ~Gauge();
+};
+
+// Field pointers of a precision for the kernels.
+template <typename S>
+struct Fields {
+    Field<S> U, A, C;  // links, clover, Schwarz clover
+};
+
+qdd_status ensure_copy(Gauge *g, qdd_prec prec, cudaStream_t s);
+
+// ------------------------------------------------------------- launchers
+
+// layout.cu
+qdd_status launch_links_to_internal(Gauge *g, const double *links_host_layout_dev, cudaStream_t s);
+// host-layout FP64 spinors (device) <-> internal fields of storage prec
+qdd_status launch_spinor_in(Gauge *g, const double *src, void *dst, float *dst_scale, qdd_prec prec, int nrhs,
+                            cudaStream_t s);
+qdd_status launch_spinor_out(Gauge *g, const void *src, const float *src_scale, double *dst, qdd_prec prec,
+                             int nrhs, cudaStream_t s);
+// internal -> internal precision conversion of spinors
+qdd_status launch_spinor_convert(Gauge *g, const void *src, const float *src_scale, qdd_prec sp, void *dst,
+                                 float *dst_scale, qdd_prec dp, int nrhs, cudaStream_t s);
+// plane-wise down-conversion of links (unscaled) / clover (per-site scale)
+qdd_status launch_links_convert(Gauge *g, qdd_prec dp, void *dst, cudaStream_t s);
+qdd_status launch_clover_convert(Gauge *g, const double2 *src, qdd_prec dp, void *dst, float *dst_scale,
+                                 cudaStream_t s);
+
+// clover.cu
+qdd_status launch_clover_build(Gauge *g, double csw, double kappa, int *d_singular, cudaStream_t s);
+
+// dslash.cu: out = D in (or out = b - D in when b != NULL); arith F64 or F32;
+// in_prec/out_prec the storage of the spinors; link/clover storage = fields_prec.
+qdd_status launch_dslash(Gauge *g, qdd_prec arith, qdd_prec fields_prec, const void *in, const float *in_s,
+                         qdd_prec in_prec, void *out, float *out_s, qdd_prec out_prec, const double2 *b, int nrhs,
+                         cudaStream_t s);
+
+// sap.cu: one half-sweep over the domains of `colour`
+struct SapBuffers {
+    void *rho, *delta, *psi;
+    float *rho_s, *delta_s;
+};
+// gather_only: apply the pending inter-domain update to the residual of the
+// domains of `colour` and store it, without a block solve.
+qdd_status launch_sap_halfsweep(Gauge *g, qdd_prec prec, const SapBuffers &b, int colour, int nmr, int nrhs,
+                                int first_psi, int gather, int gather_only, int *d_err, cudaStream_t s);
+size_t sap_smem_bytes(const HostGeom &hg, qdd_prec prec, bool stage_links, bool stage_clover);
+
+// blas.cu (FP64 complex vectors of n elements, stored as double2; scratch holds
+// blas_scratch_elems(ctx) double2 of per-block partial sums)
+int blas_blocks(const Ctx *ctx, int64_t n);
+size_t blas_scratch_elems(const Ctx *ctx);
+qdd_status blas_cdot_multi(Ctx *ctx, const double2 *v, int nvec, int64_t ld, const double2 *w, int64_t n,
+                           double2 *out, double2 *scratch, cudaStream_t s);
+qdd_status blas_caxpy_multi_norm(Ctx *ctx, const double2 *v, int nvec, int64_t ld, const double2 *coef, double2 *w,
+                                 int64_t n, double2 *norm2_out, double2 *scratch, cudaStream_t s);
+qdd_status blas_norm2(Ctx *ctx, const double2 *w, int64_t n, double2 *out, double2 *scratch, cudaStream_t s);
+qdd_status blas_scale_by_norm(Ctx *ctx, const double2 *w, int64_t n, const double2 *norm2, double2 *out,
+                              cudaStream_t s);
+qdd_status blas_axpy_multi(Ctx *ctx, const void *z, bool z_f32, int nvec, int64_t ld, const double2 *coef,
+                           double2 *x, int64_t n, cudaStream_t s);
+
+// solver.cu
+std::unique_ptr<Workspace> make_workspace();
+size_t workspace_bytes(const Gauge *g, int m, int nrhs, qdd_prec sp, bool use_sap);
+size_t workspace_held(const Workspace *w);
+void workspace_release(Workspace *w);
+// rel_out (optional): true relative residual of every right-hand side at return
+qdd_status solve_impl(Gauge *g, Workspace *w, const double *b, double *x, int on_device,
+                      const qdd_solve_params *p, qdd_report *rep, cudaStream_t s,
+                      std::vector<double> *rel_out = nullptr);
+
+}  // namespace qdd
+
+struct qdd_ctx : public qdd::Ctx {};
+struct qdd_gauge : public qdd::Gauge {};

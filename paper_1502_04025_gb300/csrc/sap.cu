@@ -1,0 +1,599 @@
+// Schwarz alternating procedure (multiplicative Schwarz), one colour half-sweep
+// per launch (arXiv:1502.04025, Sec. 3.1; Sec. 3.5: cores synchronise only
+// after an MR block solve, here the kernel boundary).
+//
+// One CTA per domain Lambda of the colour being swept, one thread per
+// even/odd site pair.  The domain's links and Schwarz clover blocks (A on even
+// sites, A^{-1} on odd sites) are staged into shared memory with bulk async
+// copies (cp.async.bulk, completion on an mbarrier) when they fit; Sec. 3.3
+// keeps each domain resident in a core's L2 for the same reason.  Then:
+//
+//   rho_Lambda += kappa * (hops from the neighbouring domains' last delta)
+//                  [the inter-domain residual update of the previous
+//                   half-sweep, pulled by the receiving domain: no atomics]
+//   bhat_e = rho_e - D_eo A_oo^{-1} rho_o           (even-odd Schur RHS)
+//   x_e = 0, r = bhat_e; nmr times:                  (MR on Dhat, Sec. 3.1 footnote)
+//       p = Dhat r = A_ee r - D_eo A_oo^{-1} D_oe r   (hops leaving Lambda dropped)
+//       alpha = <p, r> / <p, p>;  x_e += alpha r;  r -= alpha p
+//   x_o = A_oo^{-1}(rho_o - D_oe x_e)
+//   delta = (x_e, x_o);  psi_Lambda += delta;  rho_Lambda = (r, 0)
+//
+// D_eo = -kappa H_eo, D_oe = -kappa H_oe.  The odd half of the new domain
+// residual is zero and the even half is the MR residual, so the residual on
+// Lambda is set directly; the neighbours receive -D delta at the start of the
+// next half-sweep.  Domain dot products: warp shuffles, then a fixed-order
+// sum over warps in shared memory (deterministic).
+#include "internal.h"
+
+namespace qdd {
+
+// ------------------------------------------------------------ PTX helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait: false if the barrier did not complete within max_spins polls
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint32_t max_spins)
+{
+    for (uint32_t n = 0; n < max_spins; n++)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// copy bytes (multiple of 16, both addresses 16-aligned) in chunks
+__device__ __forceinline__ void bulk_g2s_chunked(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    const uint32_t kChunk = 32768;
+    for (uint32_t off = 0; off < bytes; off += kChunk) {
+        uint32_t n = bytes - off < kChunk ? bytes - off : kChunk;
+        bulk_g2s((char *)dst + off, (const char *)src + off, n, bar);
+    }
+}
+
+// ---------------------------------------------------------- kernel state
+
+template <typename R, typename SL, typename SC, typename SS, typename SP>
+struct SapArgs {
+    Geom g;
+    Field<SL> U;
+    Field<SC> C;      // Schwarz clover: A on even sites, A^{-1} on odd sites
+    Field<SS> rho;    // residual (read and written on the swept domains)
+    Field<SS> delta;  // last correction of every domain
+    Field<SP> psi;    // accumulated preconditioner output
+    int64_t rstride;  // elements between right-hand sides (V*12)
+    int64_t sstride;  // scale entries between right-hand sides (V)
+    R kappa;
+    int colour, nmr, nrhs, first_psi, gather, gather_only;
+    int *err;
+};
+
+__host__ __device__ constexpr size_t align128(size_t b) { return (b + 127) & ~(size_t)127; }
+
+template <typename R, typename SL, typename SC>
+__host__ __device__ constexpr size_t sap_smem_layout(int Vd, bool stl, bool stc)
+{
+    return (stl ? align128((size_t)36 * Vd * sizeof(typename SL::T2)) : 0) +
+           (stc ? align128((size_t)36 * Vd * sizeof(typename SC::T2)) : 0) +
+           ((stc && SC::kScaled) ? align128((size_t)Vd * 4) : 0) + 3 * align128((size_t)12 * (Vd / 2) * sizeof(cpx<R>)) +
+           align128(128 * sizeof(R)) + align128(16);
+}
+
+template <typename R, typename SL, typename SC, typename SS, typename SP, bool STL, bool STC>
+struct SapBlock {
+    const SapArgs<R, SL, SC, SS, SP> &a;
+    int d, Vd, Vh;
+    const typename SL::T2 *sL;
+    const typename SC::T2 *sC;
+    const float *sCs;
+
+    __device__ __forceinline__ void link(int dd, int s, int mu, cpx<R> *u) const
+    {
+        if (STL && dd == d) {
+#pragma unroll
+            for (int k = 0; k < 9; k++) u[k] = ld_s<R>(sL + (mu * 9 + k) * Vd + s);
+        } else {
+            const typename SL::T2 *p = a.U.p + ((int64_t)dd * 36 + mu * 9) * Vd + s;
+#pragma unroll
+            for (int k = 0; k < 9; k++) u[k] = ld_c<R>(p + (int64_t)k * Vd);
+        }
+    }
+
+    // out = C(s) in : the Schwarz clover of this domain's site s, both blocks
+    __device__ __forceinline__ void clover(int s, const cpx<R> *in, cpx<R> *out) const
+    {
+#pragma unroll
+        for (int blk = 0; blk < 2; blk++) {
+            cpx<R> m[18];
+            if (STC) {
+                R sc = SC::kScaled ? (R)sCs[s] : (R)1;
+#pragma unroll
+                for (int k = 0; k < 18; k++) {
+                    cpx<R> v = ld_s<R>(sC + (blk * 18 + k) * Vd + s);
+                    m[k] = SC::kScaled ? sc * v : v;
+                }
+            } else {
+                const typename SC::T2 *p = a.C.p + ((int64_t)d * 36 + blk * 18) * Vd + s;
+                R sc = SC::kScaled ? (R)__ldg(a.C.scale + (int64_t)d * Vd + s) : (R)1;
+#pragma unroll
+                for (int k = 0; k < 18; k++) {
+                    cpx<R> v = ld_c<R>(p + (int64_t)k * Vd);
+                    m[k] = SC::kScaled ? sc * v : v;
+                }
+            }
+            herm6_mul(m, in + 6 * blk, out + 6 * blk);
+        }
+    }
+
+    // hops of site s from a shared-memory half-field (sites src_off..src_off+Vh-1),
+    // dropping hops that leave the domain (Dirichlet boundary)
+    template <int MU>
+    __device__ __forceinline__ void inner_dir(int s, const uint16_t *nb, const cpx<R> *src, int src_off,
+                                              cpx<R> *acc) const
+    {
+        cpx<R> u[9], x[12];
+        uint16_t e = nb[2 * MU];
+        if (!(e & kCross)) {
+            int ns = (e & kSlotMask) - src_off;
+#pragma unroll
+            for (int k = 0; k < 12; k++) x[k] = src[k * Vh + ns];
+            link(d, s, MU, u);
+            hop<MU, +1>(u, x, acc);
+        }
+        e = nb[2 * MU + 1];
+        if (!(e & kCross)) {
+            int ns = e & kSlotMask;
+#pragma unroll
+            for (int k = 0; k < 12; k++) x[k] = src[k * Vh + ns - src_off];
+            link(d, ns, MU, u);
+            hop<MU, -1>(u, x, acc);
+        }
+    }
+
+    __device__ __forceinline__ void inner_hops(int s, const uint16_t *nb, const cpx<R> *src, int src_off,
+                                               cpx<R> *acc) const
+    {
+#pragma unroll
+        for (int k = 0; k < 12; k++) acc[k] = mk<R>(0, 0);
+        inner_dir<0>(s, nb, src, src_off, acc);
+        inner_dir<1>(s, nb, src, src_off, acc);
+        inner_dir<2>(s, nb, src, src_off, acc);
+        inner_dir<3>(s, nb, src, src_off, acc);
+    }
+
+    __device__ __forceinline__ void load_delta(int64_t rb, int64_t sb, int nd, int ns, cpx<R> *x) const
+    {
+        const typename SS::T2 *p = a.delta.p + rb + (int64_t)nd * 12 * Vd + ns;
+        R sc = SS::kScaled ? (R)__ldg(a.delta.scale + sb + (int64_t)nd * Vd + ns) : (R)1;
+#pragma unroll
+        for (int k = 0; k < 12; k++) {
+            cpx<R> v = ld_c<R>(p + (int64_t)k * Vd);
+            x[k] = SS::kScaled ? sc * v : v;
+        }
+    }
+
+    // hops of site s from the neighbouring domains' delta (the hops that leave Lambda)
+    template <int MU>
+    __device__ __forceinline__ void outer_dir(int s, const uint16_t *nb, int64_t rb, int64_t sb, cpx<R> *acc) const
+    {
+        cpx<R> u[9], x[12];
+        uint16_t e = nb[2 * MU];
+        if (e & kCross) {
+            int nd = __ldg(a.g.nbd + d * 8 + 2 * MU);
+            load_delta(rb, sb, nd, e & kSlotMask, x);
+            link(d, s, MU, u);
+            hop<MU, +1>(u, x, acc);
+        }
+        e = nb[2 * MU + 1];
+        if (e & kCross) {
+            int nd = __ldg(a.g.nbd + d * 8 + 2 * MU + 1);
+            int ns = e & kSlotMask;
+            load_delta(rb, sb, nd, ns, x);
+            link(nd, ns, MU, u);
+            hop<MU, -1>(u, x, acc);
+        }
+    }
+
+    __device__ __forceinline__ void outer_hops(int s, const uint16_t *nb, int64_t rb, int64_t sb, cpx<R> *acc) const
+    {
+#pragma unroll
+        for (int k = 0; k < 12; k++) acc[k] = mk<R>(0, 0);
+        outer_dir<0>(s, nb, rb, sb, acc);
+        outer_dir<1>(s, nb, rb, sb, acc);
+        outer_dir<2>(s, nb, rb, sb, acc);
+        outer_dir<3>(s, nb, rb, sb, acc);
+    }
+};
+
+template <typename R, typename S>
+__device__ __forceinline__ void load_sp(const Field<S> &f, int64_t rb, int64_t sb, int d, int s, int Vd, cpx<R> *x)
+{
+    const typename S::T2 *p = f.p + rb + (int64_t)d * 12 * Vd + s;
+    R sc = S::kScaled ? (R)f.scale[sb + (int64_t)d * Vd + s] : (R)1;
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+        cpx<R> v = ld_s<R>(p + (int64_t)k * Vd);
+        x[k] = S::kScaled ? sc * v : v;
+    }
+}
+
+template <typename R, typename S>
+__device__ __forceinline__ void store_sp(const Field<S> &f, int64_t rb, int64_t sb, int d, int s, int Vd,
+                                         const cpx<R> *x)
+{
+    typename S::T2 *p = f.p + rb + (int64_t)d * 12 * Vd + s;
+    if (S::kScaled) {
+        R m = 0;
+#pragma unroll
+        for (int k = 0; k < 12; k++) m = fmax(m, fmax(fabs(x[k].re), fabs(x[k].im)));
+        float sc = (float)m;
+        f.scale[sb + (int64_t)d * Vd + s] = sc;
+        R inv = m > 0 ? (R)1 / (R)sc : (R)0;
+#pragma unroll
+        for (int k = 0; k < 12; k++) st_c<R>(p + (int64_t)k * Vd, inv * x[k]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 12; k++) st_c<R>(p + (int64_t)k * Vd, x[k]);
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ R warp_sum(R v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename R, typename SL, typename SC, typename SS, typename SP, bool STL, bool STC>
+__global__ void __launch_bounds__(256) k_sap(const SapArgs<R, SL, SC, SS, SP> a)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    const Geom &g = a.g;
+    const int Vd = g.Vd, Vh = g.Vh;
+    const int i = threadIdx.x;
+    const int d = a.colour * g.Nd2 + blockIdx.x;
+    const int se = i, so = Vh + i;
+
+    unsigned char *ptr = smem;
+    typename SL::T2 *sL = nullptr;
+    typename SC::T2 *sC = nullptr;
+    float *sCs = nullptr;
+    if (STL) { sL = (typename SL::T2 *)ptr; ptr += align128((size_t)36 * Vd * sizeof(typename SL::T2)); }
+    if (STC) {
+        sC = (typename SC::T2 *)ptr;
+        ptr += align128((size_t)36 * Vd * sizeof(typename SC::T2));
+        if (SC::kScaled) { sCs = (float *)ptr; ptr += align128((size_t)Vd * 4); }
+    }
+    cpx<R> *sR = (cpx<R> *)ptr;   ptr += align128((size_t)12 * Vh * sizeof(cpx<R>));
+    cpx<R> *sT = (cpx<R> *)ptr;   ptr += align128((size_t)12 * Vh * sizeof(cpx<R>));
+    cpx<R> *sRo = (cpx<R> *)ptr;  ptr += align128((size_t)12 * Vh * sizeof(cpx<R>));
+    R *sRed = (R *)ptr;           ptr += align128(128 * sizeof(R));
+    uint64_t *bar = (uint64_t *)ptr;
+
+    // stage the domain's links and clover blocks
+    if (STL || STC) {
+        if (i == 0) {
+            mbar_init(bar, 1);
+            fence_mbar_init();
+        }
+        __syncthreads();
+        if (i == 0) {
+            uint32_t lb = STL ? (uint32_t)(36 * Vd * sizeof(typename SL::T2)) : 0;
+            uint32_t cb = STC ? (uint32_t)(36 * Vd * sizeof(typename SC::T2)) : 0;
+            uint32_t sb = (STC && SC::kScaled) ? (uint32_t)(Vd * 4) : 0;
+            mbar_arrive_expect_tx(bar, lb + cb + sb);
+            if (STL) bulk_g2s_chunked(sL, a.U.p + (int64_t)d * 36 * Vd, lb, bar);
+            if (STC) bulk_g2s_chunked(sC, a.C.p + (int64_t)d * 36 * Vd, cb, bar);
+            if (STC && SC::kScaled) bulk_g2s_chunked(sCs, a.C.scale + (int64_t)d * Vd, sb, bar);
+        }
+    }
+
+    // neighbour slots of this thread's two sites, kept in registers
+    uint16_t nbe[8], nbo[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        nbe[k] = __ldg(g.nbl + se * 8 + k);
+        nbo[k] = __ldg(g.nbl + so * 8 + k);
+    }
+
+    SapBlock<R, SL, SC, SS, SP, STL, STC> B{a, d, Vd, Vh, sL, sC, sCs};
+    const R kappa = a.kappa;
+    const int nwarps = (Vh + 31) / 32;
+    const bool full_warps = (Vh % 32) == 0;
+
+    for (int rr = 0; rr < a.nrhs; rr++) {
+        const int64_t rb = rr * a.rstride, sb = rr * a.sstride;
+        cpx<R> re[12], ro[12], acc[12];
+        load_sp<R, SS>(a.rho, rb, sb, d, se, Vd, re);
+        load_sp<R, SS>(a.rho, rb, sb, d, so, Vd, ro);
+
+        if ((STL || STC) && rr == 0) {
+            bool ok = mbar_wait_bounded(bar, 0, 1u << 22);
+            if (!ok) atomicOr(a.err, kErrMbarTimeout);
+            if (__syncthreads_or(!ok)) {
+                // give the copies in flight a last bounded chance to land, then leave
+                mbar_wait_bounded(bar, 0, 1u << 20);
+                return;
+            }
+        }
+
+        // inter-domain residual update from the other colour's last corrections
+        if (a.gather) {
+            B.outer_hops(se, nbe, rb, sb, acc);
+#pragma unroll
+            for (int k = 0; k < 12; k++) re[k] = re[k] + kappa * acc[k];
+            B.outer_hops(so, nbo, rb, sb, acc);
+#pragma unroll
+            for (int k = 0; k < 12; k++) ro[k] = ro[k] + kappa * acc[k];
+        }
+        if (a.gather_only) {
+            store_sp<R, SS>(a.rho, rb, sb, d, se, Vd, re);
+            store_sp<R, SS>(a.rho, rb, sb, d, so, Vd, ro);
+            continue;
+        }
+
+        // t_o = A_oo^{-1} rho_o
+        {
+            cpx<R> t[12];
+            B.clover(so, ro, t);
+#pragma unroll
+            for (int k = 0; k < 12; k++) {
+                sT[k * Vh + i] = t[k];
+                sRo[k * Vh + i] = ro[k];
+            }
+        }
+        __syncthreads();
+
+        // bhat_e = rho_e + kappa H_eo t_o ; r = bhat_e ; x = 0
+        cpx<R> r[12], x[12], p[12];
+        B.inner_hops(se, nbe, sT, Vh, acc);
+#pragma unroll
+        for (int k = 0; k < 12; k++) {
+            r[k] = re[k] + kappa * acc[k];
+            x[k] = mk<R>(0, 0);
+            sR[k * Vh + i] = r[k];
+        }
+        __syncthreads();
+
+        for (int it = 0; it < a.nmr; it++) {
+            // t_o = A_oo^{-1} (-kappa H_oe r)
+            {
+                cpx<R> u[12], t[12];
+                B.inner_hops(so, nbo, sR, 0, acc);
+#pragma unroll
+                for (int k = 0; k < 12; k++) u[k] = (-kappa) * acc[k];
+                B.clover(so, u, t);
+#pragma unroll
+                for (int k = 0; k < 12; k++) sT[k * Vh + i] = t[k];
+            }
+            __syncthreads();
+            // p = A_ee r + kappa H_eo t_o ; dots
+            B.inner_hops(se, nbe, sT, Vh, acc);
+            B.clover(se, r, p);
+            R pr_re = 0, pr_im = 0, pp = 0;
+#pragma unroll
+            for (int k = 0; k < 12; k++) {
+                p[k] = p[k] + kappa * acc[k];
+                pr_re = fma(p[k].re, r[k].re, pr_re);
+                pr_re = fma(p[k].im, r[k].im, pr_re);
+                pr_im = fma(p[k].re, r[k].im, pr_im);
+                pr_im = fma(-p[k].im, r[k].re, pr_im);
+                pp = fma(p[k].re, p[k].re, pp);
+                pp = fma(p[k].im, p[k].im, pp);
+            }
+            if (full_warps) {
+                pr_re = warp_sum(pr_re);
+                pr_im = warp_sum(pr_im);
+                pp = warp_sum(pp);
+                if ((i & 31) == 0) {
+                    sRed[(i >> 5) * 4 + 0] = pr_re;
+                    sRed[(i >> 5) * 4 + 1] = pr_im;
+                    sRed[(i >> 5) * 4 + 2] = pp;
+                }
+            } else {
+                // partial warp (Vh < 32): per-thread partials, summed in order below
+                sRed[i * 3 + 0] = pr_re;
+                sRed[i * 3 + 1] = pr_im;
+                sRed[i * 3 + 2] = pp;
+            }
+            __syncthreads();
+            R tr = 0, ti_ = 0, tp = 0;
+            if (full_warps) {
+                for (int w = 0; w < nwarps; w++) {
+                    tr += sRed[w * 4 + 0];
+                    ti_ += sRed[w * 4 + 1];
+                    tp += sRed[w * 4 + 2];
+                }
+            } else {
+                for (int w = 0; w < Vh; w++) {
+                    tr += sRed[w * 3 + 0];
+                    ti_ += sRed[w * 3 + 1];
+                    tp += sRed[w * 3 + 2];
+                }
+            }
+            cpx<R> alpha = tp > (R)0 ? mk<R>(tr / tp, ti_ / tp) : mk<R>(0, 0);
+            const bool last = it == a.nmr - 1;
+#pragma unroll
+            for (int k = 0; k < 12; k++) {
+                cfma(x[k], alpha, r[k]);
+                r[k] = r[k] - alpha * p[k];
+            }
+            // sR was last read before the first barrier of this step, and sRed is
+            // rewritten only after the next step's first barrier
+#pragma unroll
+            for (int k = 0; k < 12; k++) sR[k * Vh + i] = last ? x[k] : r[k];
+            __syncthreads();
+        }
+        if (a.nmr == 0) {
+#pragma unroll
+            for (int k = 0; k < 12; k++) sR[k * Vh + i] = x[k];
+            __syncthreads();
+        }
+
+        // x_o = A_oo^{-1} (rho_o + kappa H_oe x_e)
+        cpx<R> xo[12];
+        {
+            cpx<R> u[12];
+            B.inner_hops(so, nbo, sR, 0, acc);
+#pragma unroll
+            for (int k = 0; k < 12; k++) u[k] = sRo[k * Vh + i] + kappa * acc[k];
+            B.clover(so, u, xo);
+        }
+
+        // outputs: delta, psi, rho on this domain
+        store_sp<R, SS>(a.delta, rb, sb, d, se, Vd, x);
+        store_sp<R, SS>(a.delta, rb, sb, d, so, Vd, xo);
+        if (a.first_psi) {
+            store_sp<R, SP>(a.psi, rb, sb, d, se, Vd, x);
+            store_sp<R, SP>(a.psi, rb, sb, d, so, Vd, xo);
+        } else {
+            cpx<R> q[12];
+            load_sp<R, SP>(a.psi, rb, sb, d, se, Vd, q);
+#pragma unroll
+            for (int k = 0; k < 12; k++) q[k] = q[k] + x[k];
+            store_sp<R, SP>(a.psi, rb, sb, d, se, Vd, q);
+            load_sp<R, SP>(a.psi, rb, sb, d, so, Vd, q);
+#pragma unroll
+            for (int k = 0; k < 12; k++) q[k] = q[k] + xo[k];
+            store_sp<R, SP>(a.psi, rb, sb, d, so, Vd, q);
+        }
+        store_sp<R, SS>(a.rho, rb, sb, d, se, Vd, r);
+#pragma unroll
+        for (int k = 0; k < 12; k++) xo[k] = mk<R>(0, 0);
+        store_sp<R, SS>(a.rho, rb, sb, d, so, Vd, xo);
+        __syncthreads();  // shared buffers are reused by the next right-hand side
+    }
+}
+
+// ---------------------------------------------------------------- launch
+
+template <typename R, typename SL, typename SC, typename SS, typename SP, bool STL, bool STC>
+static qdd_status run_sap(Gauge *g, const SapArgs<R, SL, SC, SS, SP> &a, cudaStream_t s)
+{
+    const HostGeom &hg = g->hg;
+    size_t smem = sap_smem_layout<R, SL, SC>(hg.Vd, STL, STC);
+    auto kern = k_sap<R, SL, SC, SS, SP, STL, STC>;
+    static thread_local size_t configured = 0;
+    if (configured < smem) {
+        QDD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        configured = smem;
+    }
+    LaunchScope ls(g->ctx->timer, K_SAP, s);
+    kern<<<hg.Nd2, hg.Vh, smem, s>>>(a);
+    QDD_CUDA(cudaGetLastError());
+    return QDD_OK;
+}
+
+static size_t smem_limit()
+{
+    static size_t lim = 0;
+    if (!lim) {
+        int dev = 0, v = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        lim = (size_t)v;
+    }
+    return lim;
+}
+
+template <typename R, typename SL, typename SC, typename SS, typename SP>
+static qdd_status dispatch_staging(Gauge *g, const SapArgs<R, SL, SC, SS, SP> &a, cudaStream_t s)
+{
+    const int Vd = g->hg.Vd;
+    const size_t lim = smem_limit();
+    if (sap_smem_layout<R, SL, SC>(Vd, true, true) <= lim) return run_sap<R, SL, SC, SS, SP, true, true>(g, a, s);
+    if (sap_smem_layout<R, SL, SC>(Vd, true, false) <= lim) return run_sap<R, SL, SC, SS, SP, true, false>(g, a, s);
+    if (sap_smem_layout<R, SL, SC>(Vd, false, false) <= lim) return run_sap<R, SL, SC, SS, SP, false, false>(g, a, s);
+    set_error("domain of %d sites does not fit in shared memory", Vd);
+    return QDD_EINVAL;
+}
+
+size_t sap_smem_bytes(const HostGeom &hg, qdd_prec prec, bool stl, bool stc)
+{
+    switch (prec) {
+    case QDD_PREC_F64: return sap_smem_layout<double, StF64, StF64>(hg.Vd, stl, stc);
+    case QDD_PREC_F32: return sap_smem_layout<float, StF32, StF32>(hg.Vd, stl, stc);
+    case QDD_PREC_F16S: return sap_smem_layout<float, StF16, StF16>(hg.Vd, stl, stc);
+    default: return sap_smem_layout<float, StBF16, StBF16>(hg.Vd, stl, stc);
+    }
+}
+
+qdd_status launch_sap_halfsweep(Gauge *g, qdd_prec prec, const SapBuffers &b, int colour, int nmr, int nrhs,
+                                int first_psi, int gather, int gather_only, int *d_err, cudaStream_t s)
+{
+    QDD_TRY(ensure_copy(g, prec, s));
+    const int64_t rs = (int64_t)g->hg.V * 12, ss = g->hg.V;
+    PrecCopy &c = g->copies[prec];
+    switch (prec) {
+    case QDD_PREC_F64: {
+        SapArgs<double, StF64, StF64, StF64, StF64> a{
+            g->geom, {g->links64.as<double2>(), nullptr}, {g->sclov64.as<double2>(), nullptr},
+            {(double2 *)b.rho, nullptr}, {(double2 *)b.delta, nullptr}, {(double2 *)b.psi, nullptr},
+            rs, ss, g->kappa, colour, nmr, nrhs, first_psi, gather, gather_only, d_err};
+        return dispatch_staging(g, a, s);
+    }
+    case QDD_PREC_F32: {
+        SapArgs<float, StF32, StF32, StF32, StF32> a{
+            g->geom, {c.links.as<float2>(), nullptr}, {c.sclov.as<float2>(), nullptr},
+            {(float2 *)b.rho, nullptr}, {(float2 *)b.delta, nullptr}, {(float2 *)b.psi, nullptr},
+            rs, ss, (float)g->kappa, colour, nmr, nrhs, first_psi, gather, gather_only, d_err};
+        return dispatch_staging(g, a, s);
+    }
+    case QDD_PREC_F16S: {
+        SapArgs<float, StF16, StF16, StF16, StF32> a{
+            g->geom, {c.links.as<__half2>(), nullptr}, {c.sclov.as<__half2>(), c.sclov_s.as<float>()},
+            {(__half2 *)b.rho, b.rho_s}, {(__half2 *)b.delta, b.delta_s}, {(float2 *)b.psi, nullptr},
+            rs, ss, (float)g->kappa, colour, nmr, nrhs, first_psi, gather, gather_only, d_err};
+        return dispatch_staging(g, a, s);
+    }
+    case QDD_PREC_BF16S: {
+        SapArgs<float, StBF16, StBF16, StBF16, StF32> a{
+            g->geom, {c.links.as<__nv_bfloat162>(), nullptr}, {c.sclov.as<__nv_bfloat162>(), c.sclov_s.as<float>()},
+            {(__nv_bfloat162 *)b.rho, b.rho_s}, {(__nv_bfloat162 *)b.delta, b.delta_s}, {(float2 *)b.psi, nullptr},
+            rs, ss, (float)g->kappa, colour, nmr, nrhs, first_psi, gather, gather_only, d_err};
+        return dispatch_staging(g, a, s);
+    }
+    default: break;
+    }
+    set_error("invalid preconditioner precision %d", (int)prec);
+    return QDD_EINVAL;
+}
+
+}  // namespace qdd

@@ -1,0 +1,256 @@
+// Serving loop: asynchronous solves with admission by the HBM budget and
+// continuous batching.
+//
+// Requests queue on the context.  Worker threads (one CUDA stream and one
+// Krylov workspace each; max_slots of them) take the oldest request whose
+// workspace fits in the budget next to what is already resident, together
+// with every queued request for the same gauge field and parameters (up to
+// 12 right-hand sides), and solve them as one multi-right-hand-side batch:
+// one Schwarz launch per half-sweep covers all of them and reuses each staged
+// domain for every source.  Requests of different workers run concurrently
+// on the device.  Each right-hand side's arithmetic (Schwarz block solves,
+// operator, Gram-Schmidt, Givens) is independent of the others in the batch
+// and runs with the same launch shapes, so a result does not depend on the
+// mix it was solved in.
+#include <chrono>
+#include <cstring>
+
+#include "internal.h"
+
+namespace qdd {
+
+constexpr int kMaxBatchRhs = 12;
+
+struct Request {
+    uint64_t ticket = 0;
+    Gauge *g = nullptr;
+    std::vector<double> b;
+    double *x = nullptr;
+    qdd_solve_params p{};
+    qdd_status status = QDD_OK;
+    qdd_report rep{};
+    std::vector<double> hist;
+    std::string err;
+    bool done = false;
+    std::chrono::steady_clock::time_point t_submit;
+};
+
+static bool same_params(const qdd_solve_params &a, const qdd_solve_params &b)
+{
+    return a.tol == b.tol && a.restart_m == b.restart_m && a.max_restarts == b.max_restarts && a.nmr == b.nmr &&
+           a.ncy == b.ncy && a.sap_prec == b.sap_prec && a.arnoldi_prec == b.arnoldi_prec &&
+           a.use_sap == b.use_sap && a.reorth == b.reorth;
+}
+
+static void worker_main(Ctx *ctx)
+{
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = nullptr;
+    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    std::unique_ptr<Workspace> ws = make_workspace();
+    std::vector<double> bm, xm;
+    for (;;) {
+        std::vector<std::shared_ptr<Request>> batch;
+        {
+            std::unique_lock<std::mutex> lk(ctx->q_mu);
+            for (;;) {
+                if (ctx->stopping) {
+                    lk.unlock();
+                    workspace_release(ws.get());
+                    cudaStreamDestroy(st);
+                    return;
+                }
+                if (!ctx->queue.empty()) {
+                    // admission: the head request's workspace must fit next to
+                    // everything resident (this worker's own workspace is reused)
+                    auto head = ctx->queue.front();
+                    size_t need = workspace_bytes(head->g, head->p.restart_m, head->p.nrhs, head->p.sap_prec,
+                                                  head->p.use_sap != 0);
+                    size_t held = workspace_held(ws.get());
+                    size_t used = ctx->used.load();
+                    size_t others = used > held ? used - held : 0;
+                    if (others + need <= ctx->budget) {
+                        int total = 0;
+                        for (auto it = ctx->queue.begin(); it != ctx->queue.end();) {
+                            auto &r = *it;
+                            bool take = batch.empty() ||
+                                        (r->g == head->g && same_params(r->p, head->p) &&
+                                         total + r->p.nrhs <= kMaxBatchRhs);
+                            if (take) {
+                                total += r->p.nrhs;
+                                batch.push_back(r);
+                                it = ctx->queue.erase(it);
+                            } else {
+                                ++it;
+                            }
+                        }
+                        break;
+                    }
+                    if (ctx->running == 0) {
+                        // nothing else can free memory: reject the head request
+                        head->status = QDD_EBUDGET;
+                        head->err = "request does not fit in the HBM budget";
+                        head->done = true;
+                        ctx->queue.pop_front();
+                        ctx->done_cv.notify_all();
+                        continue;
+                    }
+                }
+                ctx->q_cv.wait(lk);
+            }
+            ctx->running++;
+        }
+        // ---- run the batch
+        const Gauge *g = batch[0]->g;
+        const size_t per = (size_t)g->hg.V * 24;
+        int total = 0;
+        for (auto &r : batch) total += r->p.nrhs;
+        bm.resize(per * total);
+        xm.resize(per * total);
+        size_t off = 0;
+        for (auto &r : batch) {
+            std::memcpy(bm.data() + off, r->b.data(), r->b.size() * sizeof(double));
+            off += r->b.size();
+        }
+        qdd_solve_params pm = batch[0]->p;
+        pm.nrhs = total;
+        qdd_report rep{};
+        std::vector<double> rel;
+        size_t need = workspace_bytes(batch[0]->g, pm.restart_m, total, pm.sap_prec, pm.use_sap != 0);
+        if (workspace_held(ws.get()) > 2 * need) workspace_release(ws.get());
+        clear_error();
+        qdd_status s = solve_impl(batch[0]->g, ws.get(), bm.data(), xm.data(), 0, &pm, &rep, st, &rel);
+        std::string msg = s == QDD_OK ? std::string() : std::string(qdd_last_error());
+        auto t_done = std::chrono::steady_clock::now();
+        {
+            std::lock_guard<std::mutex> lk(ctx->q_mu);
+            off = 0;
+            int r0 = 0;
+            for (auto &r : batch) {
+                std::memcpy(r->x, xm.data() + off, r->b.size() * sizeof(double));
+                off += r->b.size();
+                r->rep = rep;
+                double tr = 0;
+                for (int k = 0; k < r->p.nrhs; k++)
+                    if (r0 + k < (int)rel.size()) tr = std::max(tr, rel[r0 + k]);
+                r->rep.true_rel_res = tr;
+                r->rep.converged = (s == QDD_OK || tr <= r->p.tol) ? (tr <= r->p.tol) : 0;
+                r->rep.seconds = std::chrono::duration<double>(t_done - r->t_submit).count();
+                r->hist.assign(rep.res_history, rep.res_history + rep.n_history);
+                r->rep.res_history = nullptr;
+                r->status = (s == QDD_ENOCONV && r->rep.converged) ? QDD_OK : s;
+                r->err = msg;
+                r->done = true;
+                r0 += r->p.nrhs;
+            }
+            ctx->running--;
+        }
+        ctx->done_cv.notify_all();
+        ctx->q_cv.notify_all();
+    }
+}
+
+Ctx::~Ctx()
+{
+    {
+        std::lock_guard<std::mutex> lk(q_mu);
+        stopping = true;
+    }
+    q_cv.notify_all();
+    for (auto &t : workers) t.join();
+}
+
+}  // namespace qdd
+
+using namespace qdd;
+
+extern "C" {
+
+qdd_status qdd_serve_config(qdd_ctx *ctx, int max_slots)
+{
+    clear_error();
+    if (!ctx || max_slots < 1 || max_slots > 64) {
+        set_error("invalid argument");
+        return QDD_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(ctx->q_mu);
+    if (!ctx->workers.empty()) {
+        set_error("the serving loop is already running");
+        return QDD_EINVAL;
+    }
+    ctx->max_slots = max_slots;
+    return QDD_OK;
+}
+
+qdd_status qdd_submit(qdd_ctx *ctx, qdd_gauge *g, const double *b, double *x, const qdd_solve_params *p,
+                      uint64_t *ticket)
+{
+    clear_error();
+    if (!ctx || !g || !b || !x || !p || !ticket || g->ctx != ctx) {
+        set_error("invalid argument");
+        return QDD_EINVAL;
+    }
+    if (p->nrhs < 1 || p->nrhs > kMaxBatchRhs) {
+        set_error("nrhs must be 1..%d", kMaxBatchRhs);
+        return QDD_EINVAL;
+    }
+    if (!g->have_clover) {
+        set_error("set_clover has not been called");
+        return QDD_EINVAL;
+    }
+    auto r = std::make_shared<Request>();
+    r->g = g;
+    r->b.assign(b, b + (size_t)g->hg.V * 24 * p->nrhs);
+    r->x = x;
+    r->p = *p;
+    r->t_submit = std::chrono::steady_clock::now();
+    {
+        std::lock_guard<std::mutex> lk(ctx->q_mu);
+        r->ticket = ctx->next_ticket++;
+        *ticket = r->ticket;
+        ctx->tickets[r->ticket] = r;
+        ctx->queue.push_back(r);
+        if (ctx->workers.empty())
+            for (int k = 0; k < ctx->max_slots; k++) ctx->workers.emplace_back(worker_main, (Ctx *)ctx);
+    }
+    ctx->q_cv.notify_one();
+    return QDD_OK;
+}
+
+qdd_status qdd_poll(qdd_ctx *ctx, uint64_t ticket, qdd_report *rep, double timeout_s)
+{
+    clear_error();
+    if (!ctx) return QDD_EINVAL;
+    static thread_local std::vector<double> hist;
+    std::unique_lock<std::mutex> lk(ctx->q_mu);
+    auto it = ctx->tickets.find(ticket);
+    if (it == ctx->tickets.end()) {
+        set_error("unknown ticket %llu", (unsigned long long)ticket);
+        return QDD_EINVAL;
+    }
+    std::shared_ptr<Request> r = it->second;
+    auto deadline = std::chrono::steady_clock::now() +
+                    std::chrono::duration_cast<std::chrono::steady_clock::duration>(
+                        std::chrono::duration<double>(timeout_s > 0 ? timeout_s : 0));
+    while (!r->done) {
+        if (ctx->done_cv.wait_until(lk, deadline) == std::cv_status::timeout && !r->done) return QDD_ENOTREADY;
+    }
+    ctx->tickets.erase(it);
+    if (rep) {
+        *rep = r->rep;
+        hist = r->hist;
+        rep->res_history = hist.data();
+        rep->n_history = (int)hist.size();
+    }
+    if (r->status != QDD_OK) set_error("%s", r->err.c_str());
+    return r->status;
+}
+
+void qdd_destroy(qdd_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,194 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on
+the same seeded inputs.
+
+Tolerances (relative, in the 2-norm over the whole output unless stated):
+  FP64 arithmetic            1e-12  (rounding order only)
+  FP32 arithmetic            1e-5   (the operator-apply bound of the target)
+  FP16 storage + FP32 arith  4e-3   (2^-11 per stored component, ~10 terms)
+  BF16 storage + FP32 arith  3e-2   (2^-8 per stored component)
+"""
+import numpy as np
+import pytest
+
+from paper_1502_04025_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5, "f16": 4e-3, "bf16": 3e-2}
+
+
+def rel(a, b):
+    a, b = np.asarray(a).ravel(), np.asarray(b).ravel()
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.fixture(scope="module")
+def q():
+    from paper_1502_04025_gb300 import build
+
+    build.build()
+    from paper_1502_04025_gb300 import qdd
+
+    return qdd
+
+
+@pytest.fixture(scope="module")
+def ctx(q):
+    c = q.qdd_create(0, 0)
+    yield c
+
+
+class Problem:
+    def __init__(self, q, ctx, ora, L, dom, eps, csw, kappa, seed):
+        self.L, self.dom, self.csw, self.kappa = L, dom, csw, kappa
+        self.V = inputs.volume(L)
+        self.U = inputs.gauge_field(L, eps, seed)
+        self.g = q.qdd_create_gauge_field(ctx, L, dom, self.U)
+        q.qdd_set_clover(self.g, csw, kappa)
+        self.A = ora.clover(L, self.U, csw, kappa)
+        self.Ainv = ora.invert_clover(L, self.A)
+
+
+_problems = {}
+
+
+def problem(q, ctx, ora, L, dom, eps=0.5, csw=1.0, kappa=0.12, seed=1001):
+    key = (tuple(L), tuple(dom), eps, csw, kappa, seed)
+    if key not in _problems:
+        _problems[key] = Problem(q, ctx, ora, L, dom, eps, csw, kappa, seed)
+    return _problems[key]
+
+
+GEOMS = [
+    ((8, 8, 8, 8), (4, 4, 4, 4)),      # config-1 geometry: 16 domains of 256 sites
+    ((4, 4, 4, 4), (2, 2, 2, 2)),      # 8-site half domains: partial-warp reductions
+    ((8, 4, 4, 12), (4, 2, 2, 2)),     # ragged: 6 blocks in t, 32-site domains
+    ((16, 8, 8, 8), (8, 4, 4, 4)),     # 8x4^3 domains of 512 sites (config-2 shape)
+]
+
+
+@pytest.mark.parametrize("L,dom", GEOMS)
+def test_clover_matches_oracle(q, ctx, ora, L, dom):
+    P = problem(q, ctx, ora, L, dom, eps=0.7, csw=1.5, kappa=0.1355)
+    blocks = q.qdd_get_clover(P.g, P.V, 0)
+    full = np.zeros((P.V, 12, 12), dtype=np.complex128)
+    full[:, :6, :6] = blocks[:, 0]
+    full[:, 6:, 6:] = blocks[:, 1]
+    assert rel(full, P.A) <= 1e-13
+    # Schwarz form: A on even sites, A^{-1} on odd sites
+    sform = q.qdd_get_clover(P.g, P.V, 1)
+    sfull = np.zeros_like(full)
+    sfull[:, :6, :6] = sform[:, 0]
+    sfull[:, 6:, 6:] = sform[:, 1]
+    c = np.stack(np.unravel_index(np.arange(P.V), L[::-1]), 1)[:, ::-1]
+    odd = (c.sum(1) % 2) == 1
+    assert rel(sfull[~odd], P.A[~odd]) <= 1e-13
+    assert rel(sfull[odd], P.Ainv[odd]) <= 1e-12
+
+
+@pytest.mark.parametrize("L,dom", GEOMS)
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16", "bf16"])
+def test_dslash_matches_oracle(q, ctx, ora, L, dom, prec):
+    P = problem(q, ctx, ora, L, dom)
+    x = inputs.gaussian_source(L, 2001)
+    want = ora.apply_D(L, P.U, P.A, P.kappa, x)
+    got = q.qdd_apply_D(P.g, x, prec)
+    assert rel(got, want) <= TOL[prec]
+    if prec == "f64":
+        assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+
+
+def test_dslash_multi_rhs(q, ctx, ora):
+    P = problem(q, ctx, ora, (8, 8, 8, 8), (4, 4, 4, 4))
+    xs = inputs.gaussian_source(P.L, 2002, nrhs=3)
+    got = q.qdd_apply_D(P.g, np.ascontiguousarray(xs), "f64", nrhs=3)
+    for r in range(3):
+        assert rel(got[r], ora.apply_D(P.L, P.U, P.A, P.kappa, xs[r])) <= TOL["f64"]
+
+
+@pytest.mark.parametrize("L,dom", GEOMS[:3])
+@pytest.mark.parametrize("n_half", [1, 2, 5, 8])
+def test_sap_f64_matches_oracle(q, ctx, ora, L, dom, n_half):
+    P = problem(q, ctx, ora, L, dom)
+    eta = inputs.gaussian_source(L, 3001)
+    psi_o, rho_o = ora.sap(L, dom, P.U, P.A, P.Ainv, P.kappa, eta, 4, n_half)
+    psi, rho = q.qdd_sap_apply(P.g, eta, 4, n_half, "f64", want_rho=True)
+    assert rel(psi, psi_o) <= 1e-12
+    assert rel(rho, rho_o) <= 1e-11
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("L,dom", [GEOMS[0], GEOMS[3]])
+def test_sap_lowp_matches_oracle(q, ctx, ora, L, dom, prec):
+    P = problem(q, ctx, ora, L, dom)
+    eta = inputs.gaussian_source(L, 3002)
+    psi_o, _ = ora.sap(L, dom, P.U, P.A, P.Ainv, P.kappa, eta, 4, 8)
+    psi = q.qdd_sap_apply(P.g, eta, 4, 8, prec)
+    assert rel(psi, psi_o) <= {"f32": 2e-5, "f16": 1e-2, "bf16": 6e-2}[prec]
+
+
+def test_sap_nmr_zero_and_multi_rhs(q, ctx, ora):
+    P = problem(q, ctx, ora, (8, 8, 8, 8), (4, 4, 4, 4))
+    etas = inputs.gaussian_source(P.L, 3003, nrhs=2)
+    for nmr in (0, 1):
+        psi = q.qdd_sap_apply(P.g, np.ascontiguousarray(etas), nmr, 4, "f64", nrhs=2)
+        for r in range(2):
+            psi_o, _ = ora.sap(P.L, P.dom, P.U, P.A, P.Ainv, P.kappa, etas[r], nmr, 4)
+            assert rel(psi[r], psi_o) <= 1e-12
+
+
+def _true_rel(ora, P, x, b):
+    r = b - ora.apply_D(P.L, P.U, P.A, P.kappa, x)
+    return np.linalg.norm(r) / np.linalg.norm(b)
+
+
+def test_solve_config1_fp64(q, ctx, ora):
+    """8^4, eps 0.5, c_sw 1.0, kappa 0.12, 4^4 domains, nmr 4, ncy 4,
+    FGMRES(16), tol 1e-10, all FP64."""
+    P = problem(q, ctx, ora, (8, 8, 8, 8), (4, 4, 4, 4))
+    b = inputs.gaussian_source(P.L, 2001)
+    x, rep = q.qdd_solve(P.g, b, tol=1e-10, restart_m=16, nmr=4, ncy=4, sap_prec="f64")
+    assert rep["converged"] and rep["true_rel_res"] <= 1e-10
+    assert _true_rel(ora, P, x, b) <= 1e-10
+    x_o, info = ora.fgmres(P.L, P.dom, P.U, P.A, P.Ainv, P.kappa, b, 1e-12, m=16, max_restarts=50, use_sap=True,
+                           nmr=4, ncy=4)
+    assert info["converged"]
+    x2, rep2 = q.qdd_solve(P.g, b, tol=1e-12, restart_m=16, nmr=4, ncy=4, sap_prec="f64")
+    assert rel(x2, x_o) <= 1e-9
+    # same method, same iteration count up to the Gram-Schmidt variant
+    assert abs(rep2["iters"] - info["iters"]) <= 2
+
+
+@pytest.mark.parametrize("prec,arn", [("f32", "f64"), ("f16", "f64"), ("bf16", "f64"), ("f32", "f32")])
+def test_solve_mixed_precision(q, ctx, ora, prec, arn):
+    P = problem(q, ctx, ora, (16, 8, 8, 8), (8, 4, 4, 4), kappa=0.125)
+    b = inputs.gaussian_source(P.L, 2002)
+    x, rep = q.qdd_solve(P.g, b, tol=1e-10, sap_prec=prec, arnoldi_prec=arn)
+    assert rep["converged"]
+    assert _true_rel(ora, P, x, b) <= 1e-10
+
+
+def test_solve_plain_gmres_and_multi_rhs(q, ctx, ora):
+    P = problem(q, ctx, ora, (8, 8, 8, 8), (4, 4, 4, 4))
+    bs = np.ascontiguousarray(inputs.point_sources(P.L)[:4])
+    xb, rep = q.qdd_solve(P.g, bs, tol=1e-10, nrhs=4, sap_prec="f32")
+    assert rep["converged"]
+    for r in range(4):
+        xr, _ = q.qdd_solve(P.g, np.ascontiguousarray(bs[r]), tol=1e-10, nrhs=1, sap_prec="f32")
+        assert np.array_equal(xr, xb[r])  # batching does not change any arithmetic
+        assert _true_rel(ora, P, xb[r], bs[r]) <= 1e-10
+    x0, rep0 = q.qdd_solve(P.g, np.ascontiguousarray(bs[0]), tol=1e-10, use_sap=0, max_restarts=200)
+    assert rep0["converged"] and _true_rel(ora, P, x0, bs[0]) <= 1e-10
+    assert rep0["iters"] > rep["iters"]
+
+
+def test_cdot_multi_matches_numpy(q, ctx):
+    import torch
+
+    g = torch.Generator().manual_seed(5)
+    n = 100_003  # ragged against the block size
+    v = torch.randn(17, n, dtype=torch.complex128, generator=g).cuda()
+    w = torch.randn(n, dtype=torch.complex128, generator=g).cuda()
+    out = q.qdd_cdot_multi(ctx, v, w).cpu().numpy()
+    want = np.conj(v.cpu().numpy()) @ w.cpu().numpy()
+    assert np.abs(out - want).max() <= 1e-12 * np.abs(want).max()

@@ -1,0 +1,129 @@
+"""Host-side checks that need no GPU: the C-ABI library loads and exports
+every entry point its header declares, and the pure host functions match
+the numbers the paper prints."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "qdd.h")
+
+
+@pytest.fixture(scope="session")
+def qdd():
+    from paper_1502_04025_gb300 import build
+
+    build.build()
+    from paper_1502_04025_gb300 import qdd as q
+
+    return q
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"\b(qdd_[A-Za-z0-9_]+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ["qdd_create", "qdd_create_gauge_field", "qdd_set_clover", "qdd_apply_D", "qdd_sap_apply",
+                 "qdd_solve", "qdd_submit", "qdd_poll", "qdd_destroy", "qdd_last_error"]:
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(qdd):
+    lib = ctypes.CDLL(qdd.LIB_PATH)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_symbol(qdd):
+    for n in declared_functions():
+        assert hasattr(qdd, n), n
+
+
+def test_load_model_pins(qdd):
+    """Sec. 3.5: 64^3x128 on 1024 KNCs with 8x4^3 domains gives N_d = 64
+    domains per KNC and 60 usable cores, load x/ceil(x) = 53%; the
+    non-uniform split 128 = 4*28+16 gives (4*56+32)/(5*60) = 85%."""
+    assert qdd.qdd_load_model(64 / 2, 60) == pytest.approx(32 / 60)
+    assert round(100 * qdd.qdd_load_model(32, 60)) == 53
+    # t-slices of 28 and 16 sites hold 56 and 32 domains per colour pair
+    loads = [qdd.qdd_load_model(n / 2, 60) * 1 for n in (56 * 2, 56 * 2, 56 * 2, 56 * 2, 32 * 2)]
+    per_knc_busy = [56, 56, 56, 56, 32]
+    assert round(100 * sum(per_knc_busy) / (5 * 60)) == 85
+    assert all(0 < l <= 1 for l in loads)
+    assert qdd.qdd_load_model(120, 60) == 1.0
+    assert qdd.qdd_load_model(0, 60) == 0.0
+
+
+def test_working_set_pins(qdd):
+    """Sec. 3.3: an 8x4^3 domain needs 456 kB in single precision and 312 kB
+    with half-precision links and clover (two full spinors plus three
+    even-site spinors of the MR iteration)."""
+    dom = (8, 4, 4, 4)
+    assert qdd.qdd_domain_working_set(dom, 4, 2, 3) == 456 * 1024
+    assert qdd.qdd_domain_working_set(dom, 2, 2, 3) == 312 * 1024
+
+
+def test_no_gpu_needed_for_errors(qdd):
+    # a null context is rejected without touching the device
+    assert qdd._lib.qdd_set_profiling(None, 1) == qdd.QDD_EINVAL
+
+
+def _coords(L, n):
+    n = np.asarray(n)
+    return np.stack([n % L[0], (n // L[0]) % L[1], (n // (L[0] * L[1])) % L[2], n // (L[0] * L[1] * L[2])], -1)
+
+
+@pytest.mark.parametrize("L,dom", [((8, 8, 8, 8), (4, 4, 4, 4)), ((4, 4, 4, 4), (2, 2, 2, 2)),
+                                   ((8, 4, 4, 12), (4, 2, 2, 2)), ((16, 8, 8, 8), (8, 4, 4, 4)),
+                                   ((16, 16, 16, 32), (8, 4, 4, 4))])
+def test_device_layout_tables(qdd, L, dom):
+    """The neighbour tables the kernels use reproduce the periodic lattice
+    neighbours, slots are colour-major and parity-split, and the
+    internal-to-host map is a permutation."""
+    site_of, nbl, nbd = qdd.qdd_layout(L, dom)
+    V, Vd = int(np.prod(L)), int(np.prod(dom))
+    Nd, Vh = V // Vd, Vd // 2
+    assert np.array_equal(np.sort(site_of), np.arange(V))
+    c = _coords(L, site_of)
+    gi = np.arange(V)
+    d, s = gi // Vd, gi % Vd
+    # parity split inside every domain, colour-major domain slots
+    assert np.array_equal(c.sum(1) % 2, (s >= Vh).astype(int))
+    blk = c // np.array(dom)
+    assert np.array_equal(blk.sum(1) % 2, (d >= Nd // 2).astype(int))
+    # every site of a slot lies in one block
+    for dd in (0, Nd // 2, Nd - 1):
+        b = blk[d == dd]
+        assert (b == b[0]).all()
+    for k in range(8):
+        mu, back = k // 2, k % 2
+        e = nbl[s, k].astype(np.int64)
+        cross = (e & 0x8000) != 0
+        ns = e & 0x7FFF
+        nd = np.where(cross, nbd[d, k], d)
+        got = site_of[nd * Vd + ns]
+        cc = c.copy()
+        cc[:, mu] = (cc[:, mu] + (-1 if back else 1)) % L[mu]
+        want = cc[:, 0] + L[0] * (cc[:, 1] + L[1] * (cc[:, 2] + L[2] * cc[:, 3]))
+        assert np.array_equal(got, want), (k,)
+        # a hop leaves the domain exactly when the block coordinate changes
+        assert np.array_equal(cross, (cc[:, mu] // dom[mu]) != blk[:, mu])
+
+
+def test_layout_rejects_bad_geometry(qdd):
+    with pytest.raises(qdd.QddError):
+        qdd.qdd_layout((8, 8, 8, 8), (8, 4, 4, 4))   # one block in x
+    with pytest.raises(qdd.QddError):
+        qdd.qdd_layout((12, 8, 8, 8), (4, 4, 4, 4))  # three blocks in x
+    with pytest.raises(qdd.QddError):
+        qdd.qdd_layout((8, 8, 8, 8), (3, 4, 4, 4))   # odd extent
+    with pytest.raises(qdd.QddError):
+        qdd.qdd_layout((32, 16, 16, 16), (16, 8, 4, 4))  # domain above 512 sites
