@@ -243,8 +243,15 @@ qdd_status qdd_create(qdd_ctx **out, int device, size_t hbm_budget_bytes)
 qdd_status qdd_set_profiling(qdd_ctx *ctx, int on)
 {
     if (!ctx) return QDD_EINVAL;
+    QDD_CUDA(cudaSetDevice(ctx->device));
     std::lock_guard<std::mutex> lk(ctx->timer.mu);
     ctx->timer.on = on != 0;
+    // create the events up front so that timed regions create none
+    while (on && ctx->timer.pool.size() < 4096) {
+        cudaEvent_t e = nullptr;
+        QDD_CUDA(cudaEventCreate(&e));
+        ctx->timer.pool.push_back(e);
+    }
     return QDD_OK;
 }
 

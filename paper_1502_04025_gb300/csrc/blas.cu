@@ -8,6 +8,8 @@
 // fixed order, one block sums them in a fixed order.  Fused forms read each
 // vector once: the multi-dot reads w once for all basis vectors, the
 // multi-axpy writes w once and returns its new norm.
+#include <type_traits>
+
 #include "internal.h"
 
 namespace qdd {
@@ -68,7 +70,7 @@ __global__ void __launch_bounds__(kBT) k_cdot_partial(const double2 *__restrict_
     if (threadIdx.x < NV) {
         double2 s = make_double2(0, 0);
         for (int ww = 0; ww < kBT / 32; ww++) s = dsum2(s, sm[ww * NV + threadIdx.x]);
-        part[(int64_t)blockIdx.x * NV + threadIdx.x] = s;
+        part[(int64_t)blockIdx.x * kNV + threadIdx.x] = s;
     }
 }
 
@@ -159,6 +161,33 @@ __global__ void __launch_bounds__(kBT) k_axpy_multi(const T2 *__restrict__ z, in
 
 // ------------------------------------------------------------- launchers
 
+// Call f with std::integral_constant<int, NV> for NV = nv (1..kNV): kernels
+// are instantiated for exactly the number of vectors they handle, because
+// predicated-off iterations of a wider unrolled loop would still occupy the
+// FP64 pipe, the bottleneck of these kernels on this GPU.
+template <typename F>
+static void nv_dispatch(int nv, F &&f)
+{
+    switch (nv) {
+    case 1: f(std::integral_constant<int, 1>{}); break;
+    case 2: f(std::integral_constant<int, 2>{}); break;
+    case 3: f(std::integral_constant<int, 3>{}); break;
+    case 4: f(std::integral_constant<int, 4>{}); break;
+    case 5: f(std::integral_constant<int, 5>{}); break;
+    case 6: f(std::integral_constant<int, 6>{}); break;
+    case 7: f(std::integral_constant<int, 7>{}); break;
+    case 8: f(std::integral_constant<int, 8>{}); break;
+    case 9: f(std::integral_constant<int, 9>{}); break;
+    case 10: f(std::integral_constant<int, 10>{}); break;
+    case 11: f(std::integral_constant<int, 11>{}); break;
+    case 12: f(std::integral_constant<int, 12>{}); break;
+    case 13: f(std::integral_constant<int, 13>{}); break;
+    case 14: f(std::integral_constant<int, 14>{}); break;
+    case 15: f(std::integral_constant<int, 15>{}); break;
+    default: f(std::integral_constant<int, 16>{}); break;
+    }
+}
+
 qdd_status blas_cdot_multi(Ctx *ctx, const double2 *v, int nvec, int64_t ld, const double2 *w, int64_t n,
                            double2 *out, double2 *scratch, cudaStream_t s)
 {
@@ -168,7 +197,9 @@ qdd_status blas_cdot_multi(Ctx *ctx, const double2 *v, int nvec, int64_t ld, con
         int nv = nvec - j0 < kNV ? nvec - j0 : kNV;
         {
             LaunchScope ls(ctx->timer, K_BLAS, s);
-            k_cdot_partial<kNV><<<nb, kBT, 0, s>>>(v + j0 * ld, nv, ld, w, n, scratch);
+            nv_dispatch(nv, [&](auto c) {
+                k_cdot_partial<decltype(c)::value><<<nb, kBT, 0, s>>>(v + j0 * ld, nv, ld, w, n, scratch);
+            });
         }
         {
             LaunchScope ls(ctx->timer, K_BLAS, s);
@@ -189,8 +220,13 @@ qdd_status blas_caxpy_multi_norm(Ctx *ctx, const double2 *v, int nvec, int64_t l
         bool last = j0 + nv >= nvec;
         {
             LaunchScope ls(ctx->timer, K_BLAS, s);
-            k_caxpy_norm<kNV><<<nb, kBT, 0, s>>>(v + j0 * ld, nv, ld, coef + j0, w, n,
-                                                  (last && norm2_out) ? scratch : nullptr);
+            double2 *part = (last && norm2_out) ? scratch : nullptr;
+            if (nv == 0)
+                k_caxpy_norm<1><<<nb, kBT, 0, s>>>(v, 0, ld, coef, w, n, part);
+            else
+                nv_dispatch(nv, [&](auto c) {
+                    k_caxpy_norm<decltype(c)::value><<<nb, kBT, 0, s>>>(v + j0 * ld, nv, ld, coef + j0, w, n, part);
+                });
         }
         j0 += nv;
     } while (j0 < nvec);
