@@ -207,6 +207,27 @@ qdd_status qdd_solve(qdd_gauge *g, const double *b, double *x, int on_device, co
 qdd_status qdd_cdot_multi(qdd_ctx *ctx, const double *v, int nvec, int64_t ld, const double *w, int64_t n,
                           double *out, void *stream);
 
+/*
+ * Allocation-free form of qdd_cdot_multi: the same multi-dot, computed by the
+ * same kernels, for callers that must not allocate device memory -- for
+ * example code whose device memory is all owned by its own pre-sized pool, or
+ * a latency-critical loop that cannot afford the device-wide synchronisation
+ * that cudaFree implies.  The paper has no counterpart; it is a service of
+ * this library.  It needs no context and calls no cudaMalloc, cudaFree or
+ * other allocating routine: its per-block partial sums live in one fixed
+ * 128 KiB device array inside the library, present on every GPU that loads
+ * the library until the process exits.  It runs on the current CUDA device.
+ * The first call on a device looks up the array's address there (once per
+ * device); make that first call before any stream capture.  Limits: nvec
+ * 1..64, n 1..2^40, ld >= n; anything else returns QDD_EINVAL with a message.
+ * All calls share the array: calls that overlap on the GPU (other streams,
+ * other host threads) race and must be serialised by the caller.  Nothing in
+ * the array needs to start at zero; each call overwrites what it reads.
+ * Arguments and layout as for qdd_cdot_multi; returns after out is written.
+ */
+qdd_status qdd_cdot_multi_noalloc(const double *v, int nvec, int64_t ld, const double *w, int64_t n,
+                                  double *out, void *stream);
+
 /* ------------------------------------------------------------- host logic */
 
 /* Average load of a colour half-sweep: x / ceil(x) with x = domains per

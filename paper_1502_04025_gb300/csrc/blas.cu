@@ -8,6 +8,7 @@
 // fixed order, one block sums them in a fixed order.  Fused forms read each
 // vector once: the multi-dot reads w once for all basis vectors, the
 // multi-axpy writes w once and returns its new norm.
+#include <mutex>
 #include <type_traits>
 
 #include "internal.h"
@@ -265,4 +266,100 @@ qdd_status blas_axpy_multi(Ctx *ctx, const void *z, bool z_f32, int nvec, int64_
     return QDD_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free multi-dot (qdd_cdot_multi_noalloc).
+//
+// The per-block partial sums live in a fixed device array that is part of the
+// library image instead of in memory from cudaMalloc.  Host code may not use
+// the array's name as a device pointer: it only stands in for the symbol, so
+// the device address is looked up once per device with cudaGetSymbolAddress
+// and passed to the kernels.  The array holds kNoAllocBlocks * kNV partials
+// (128 KiB) on every GPU that loads the library, until the process exits.
+
+constexpr int kNoAllocBlocks = 512;
+static __device__ __align__(256) double2 g_noalloc_partials[kNoAllocBlocks * kNV];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double2 *g_noalloc_ptr[kMaxDevices] = {};
+int g_noalloc_nsm[kMaxDevices] = {};
+
+// Device address of the partials array on the current device, resolved on
+// the first call for that device.
+qdd_status noalloc_setup(int dev, double2 **ptr, int *nsm)
+{
+    if (dev < 0 || dev >= kMaxDevices) {
+        set_error("device %d out of range for the allocation-free entry points", dev);
+        return QDD_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+        if (e != cudaSuccess || !p) {
+            set_error("cudaGetSymbolAddress of the partial-sum array failed on device %d: %s", dev,
+                      cudaGetErrorString(e));
+            return QDD_ECUDA;
+        }
+        int sm = 0;
+        e = cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) {
+            set_error("cudaDeviceGetAttribute failed on device %d: %s", dev, cudaGetErrorString(e));
+            return QDD_ECUDA;
+        }
+        g_noalloc_nsm[dev] = sm;
+        g_noalloc_ptr[dev] = (double2 *)p;
+    }
+    *ptr = g_noalloc_ptr[dev];
+    *nsm = g_noalloc_nsm[dev];
+    return QDD_OK;
+}
+}  // namespace
+
 }  // namespace qdd
+
+extern "C" qdd_status qdd_cdot_multi_noalloc(const double *v, int nvec, int64_t ld, const double *w, int64_t n,
+                                             double *out, void *stream)
+{
+    using namespace qdd;
+    clear_error();
+    if (!v || !w || !out) {
+        set_error("null pointer argument");
+        return QDD_EINVAL;
+    }
+    if (nvec < 1 || nvec > 64) {
+        set_error("nvec = %d outside 1..64", nvec);
+        return QDD_EINVAL;
+    }
+    if (n < 1 || n > (int64_t(1) << 40) || ld < n) {
+        set_error("vector length n = %lld (stride %lld) outside 1..2^40 or stride below n", (long long)n,
+                  (long long)ld);
+        return QDD_EINVAL;
+    }
+    int dev = 0;
+    QDD_CUDA(cudaGetDevice(&dev));
+    double2 *part = nullptr;
+    int nsm = 0;
+    QDD_TRY(noalloc_setup(dev, &part, &nsm));
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t nb64 = (n + kBT - 1) / kBT;
+    int64_t cap = 2LL * nsm;
+    if (cap > kNoAllocBlocks) cap = kNoAllocBlocks;
+    if (nb64 > cap) nb64 = cap;
+    const int nb = (int)(nb64 < 1 ? 1 : nb64);
+    const double2 *V2 = (const double2 *)v, *W2 = (const double2 *)w;
+    double2 *O2 = (double2 *)out;
+    // every block overwrites its own partials before the final sum reads them,
+    // so nothing in the shared array has to start at zero
+    for (int j0 = 0; j0 < nvec; j0 += kNV) {
+        int nv = nvec - j0 < kNV ? nvec - j0 : kNV;
+        nv_dispatch(nv, [&](auto c) {
+            k_cdot_partial<decltype(c)::value><<<nb, kBT, 0, s>>>(V2 + j0 * ld, nv, ld, W2, n, part);
+        });
+        k_reduce_final<<<nv, kBT, 0, s>>>(part, nb, kNV, O2 + j0, 0);
+    }
+    QDD_CUDA(cudaGetLastError());
+    QDD_CUDA(cudaStreamSynchronize(s));
+    return QDD_OK;
+}

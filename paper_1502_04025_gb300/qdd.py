@@ -71,6 +71,7 @@ _SIGS = {
     "qdd_solve": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.POINTER(qdd_solve_params),
                                  ctypes.POINTER(qdd_report), _vp]),
     "qdd_cdot_multi": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int64, _vp, ctypes.c_int64, _vp, _vp]),
+    "qdd_cdot_multi_noalloc": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int64, _vp, ctypes.c_int64, _vp, _vp]),
     "qdd_load_model": (ctypes.c_double, [ctypes.c_double, ctypes.c_double]),
     "qdd_domain_working_set": (ctypes.c_double, [_ip, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "qdd_layout": (ctypes.c_int, [_ip, _ip, _vp, _vp, _vp]),
@@ -248,6 +249,20 @@ def qdd_cdot_multi(ctx, v, w):
     out = torch.empty(nvec, dtype=torch.complex128, device=v.device)
     _check(_lib.qdd_cdot_multi(ctx, v.data_ptr(), nvec, v.stride(0), w.data_ptr(), n, out.data_ptr(),
                                _stream(v)), "qdd_cdot_multi")
+    return out
+
+
+def qdd_cdot_multi_noalloc(v, w, out=None):
+    """<v_i, w> without any device allocation inside the library (torch CUDA
+    complex128 tensors; out, if given, is a CUDA tensor of nvec elements)."""
+    import torch
+
+    assert v.is_cuda and w.is_cuda and v.dtype == torch.complex128 and w.dtype == torch.complex128
+    nvec, n = v.shape
+    if out is None:
+        out = torch.empty(nvec, dtype=torch.complex128, device=v.device)
+    _check(_lib.qdd_cdot_multi_noalloc(v.data_ptr(), nvec, v.stride(0), w.data_ptr(), n, out.data_ptr(),
+                                       _stream(v)), "qdd_cdot_multi_noalloc")
     return out
 
 
