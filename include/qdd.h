@@ -112,10 +112,16 @@ void qdd_destroy(qdd_ctx *ctx);
 /* Message of the last failed call on this thread ("" if none). */
 const char *qdd_last_error(void);
 
-/* Per-kernel-class device timing with CUDA events (adds an event pair around
- * every timed launch).  Results land in qdd_report's ms_* fields and in
- * qdd_get_kernel_times. */
-qdd_status qdd_set_profiling(qdd_ctx *ctx, int on);
+/* Per-kernel-class device timing with CUDA events: classes is a bit mask of
+ * QDD_PROF_* (0 = off); every launch of a selected class gets an event pair
+ * on its stream.  Launch counts are kept for every class regardless.  Results
+ * land in qdd_report's ms_* fields and in qdd_get_kernel_times. */
+#define QDD_PROF_SAP 1
+#define QDD_PROF_DSLASH 2
+#define QDD_PROF_BLAS 4
+#define QDD_PROF_OTHER 8
+#define QDD_PROF_ALL 15
+qdd_status qdd_set_profiling(qdd_ctx *ctx, int classes);
 
 /* Kernel-class timings of the context since the last reset:
  * out[0..1] = (ms, launches) of SAP block kernels, out[2..3] of full-lattice

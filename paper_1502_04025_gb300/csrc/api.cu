@@ -42,7 +42,7 @@ void Timer::begin(int cls, cudaStream_t s, cudaEvent_t *a)
 {
     std::lock_guard<std::mutex> lk(mu);
     launches[cls]++;
-    if (on) {
+    if (mask & (1 << cls)) {
         *a = get_event();
         cudaEventRecord(*a, s);
     }
@@ -240,14 +240,14 @@ qdd_status qdd_create(qdd_ctx **out, int device, size_t hbm_budget_bytes)
     return QDD_OK;
 }
 
-qdd_status qdd_set_profiling(qdd_ctx *ctx, int on)
+qdd_status qdd_set_profiling(qdd_ctx *ctx, int classes)
 {
     if (!ctx) return QDD_EINVAL;
     QDD_CUDA(cudaSetDevice(ctx->device));
     std::lock_guard<std::mutex> lk(ctx->timer.mu);
-    ctx->timer.on = on != 0;
+    ctx->timer.mask = classes & QDD_PROF_ALL;
     // create the events up front so that timed regions create none
-    while (on && ctx->timer.pool.size() < 4096) {
+    while (classes && ctx->timer.pool.size() < 4096) {
         cudaEvent_t e = nullptr;
         QDD_CUDA(cudaEventCreate(&e));
         ctx->timer.pool.push_back(e);

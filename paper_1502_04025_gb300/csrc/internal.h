@@ -47,7 +47,7 @@ enum KClass { K_SAP = 0, K_DSLASH = 1, K_BLAS = 2, K_OTHER = 3 };
 // Launch bookkeeping of a context: launch counts always, CUDA-event timing of
 // each launch when profiling is on (events resolved at sync points).
 struct Timer {
-    bool on = false;
+    int mask = 0;  // classes timed with events
     long long launches[4] = {0, 0, 0, 0};
     double ms[4] = {0, 0, 0, 0};
     long long timed[4] = {0, 0, 0, 0};

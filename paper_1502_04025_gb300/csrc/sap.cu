@@ -281,6 +281,19 @@ __device__ __forceinline__ R warp_sum(R v)
     return v;
 }
 
+// Phases of one domain visit.  Every phase runs the same code: one hop sum
+// over the sites of one parity (read from the other parity's shared-memory
+// half-field), one clover product, a short epilogue; the stencil and clover
+// code therefore appear once in the kernel, which keeps it inside the
+// instruction cache.
+enum SapPhase : int {
+    PH_SETUP_ODD = 0,   // t_o = A_oo^{-1} rho_o                      -> sT
+    PH_SETUP_EVEN = 1,  // r = rho_e + kappa H_eo t_o ; x = 0           -> sR
+    PH_MR_ODD = 2,      // t_o = A_oo^{-1} (-kappa H_oe r)              -> sT
+    PH_MR_EVEN = 3,     // p = A_ee r + kappa H_eo t_o; MR update       -> sR
+    PH_RECON_ODD = 4    // x_o = A_oo^{-1} (rho_o + kappa H_oe x_e)
+};
+
 template <typename R, typename SL, typename SC, typename SS, typename SP, bool STL, bool STC>
 __global__ void __launch_bounds__(256) k_sap(const SapArgs<R, SL, SC, SS, SP> a)
 {
@@ -301,9 +314,9 @@ __global__ void __launch_bounds__(256) k_sap(const SapArgs<R, SL, SC, SS, SP> a)
         ptr += align128((size_t)36 * Vd * sizeof(typename SC::T2));
         if (SC::kScaled) { sCs = (float *)ptr; ptr += align128((size_t)Vd * 4); }
     }
-    cpx<R> *sR = (cpx<R> *)ptr;   ptr += align128((size_t)12 * Vh * sizeof(cpx<R>));
-    cpx<R> *sT = (cpx<R> *)ptr;   ptr += align128((size_t)12 * Vh * sizeof(cpx<R>));
-    cpx<R> *sRo = (cpx<R> *)ptr;  ptr += align128((size_t)12 * Vh * sizeof(cpx<R>));
+    cpx<R> *sR = (cpx<R> *)ptr;   ptr += align128((size_t)12 * Vh * sizeof(cpx<R>));   // even half-field
+    cpx<R> *sT = (cpx<R> *)ptr;   ptr += align128((size_t)12 * Vh * sizeof(cpx<R>));   // odd half-field
+    cpx<R> *sRo = (cpx<R> *)ptr;  ptr += align128((size_t)12 * Vh * sizeof(cpx<R>));   // rho_o after inflow
     R *sRed = (R *)ptr;           ptr += align128(128 * sizeof(R));
     uint64_t *bar = (uint64_t *)ptr;
 
@@ -337,12 +350,10 @@ __global__ void __launch_bounds__(256) k_sap(const SapArgs<R, SL, SC, SS, SP> a)
     const R kappa = a.kappa;
     const int nwarps = (Vh + 31) / 32;
     const bool full_warps = (Vh % 32) == 0;
+    const int nphase = a.gather_only ? 0 : 3 + 2 * a.nmr;
 
     for (int rr = 0; rr < a.nrhs; rr++) {
         const int64_t rb = rr * a.rstride, sb = rr * a.sstride;
-        cpx<R> re[12], ro[12], acc[12];
-        load_sp<R, SS>(a.rho, rb, sb, d, se, Vd, re);
-        load_sp<R, SS>(a.rho, rb, sb, d, so, Vd, ro);
 
         if ((STL || STC) && rr == 0) {
             bool ok = mbar_wait_bounded(bar, 0, 1u << 22);
@@ -354,151 +365,158 @@ __global__ void __launch_bounds__(256) k_sap(const SapArgs<R, SL, SC, SS, SP> a)
             }
         }
 
-        // inter-domain residual update from the other colour's last corrections
-        if (a.gather) {
-            B.outer_hops(se, nbe, rb, sb, acc);
+        // residual of this domain plus the inflow from the other colour's
+        // last corrections: rho += kappa * (hops that enter the domain)
+        cpx<R> acc[12], v[12];
+        for (int par = 0; par < 2; par++) {
+            const int s = par ? so : se;
+            load_sp<R, SS>(a.rho, rb, sb, d, s, Vd, v);
+            if (a.gather) {
+                uint16_t nb[8];
 #pragma unroll
-            for (int k = 0; k < 12; k++) re[k] = re[k] + kappa * acc[k];
-            B.outer_hops(so, nbo, rb, sb, acc);
+                for (int k = 0; k < 8; k++) nb[k] = par ? nbo[k] : nbe[k];
+                B.outer_hops(s, nb, rb, sb, acc);
 #pragma unroll
-            for (int k = 0; k < 12; k++) ro[k] = ro[k] + kappa * acc[k];
-        }
-        if (a.gather_only) {
-            store_sp<R, SS>(a.rho, rb, sb, d, se, Vd, re);
-            store_sp<R, SS>(a.rho, rb, sb, d, so, Vd, ro);
-            continue;
-        }
-
-        // t_o = A_oo^{-1} rho_o
-        {
-            cpx<R> t[12];
-            B.clover(so, ro, t);
-#pragma unroll
-            for (int k = 0; k < 12; k++) {
-                sT[k * Vh + i] = t[k];
-                sRo[k * Vh + i] = ro[k];
+                for (int k = 0; k < 12; k++) v[k] = v[k] + kappa * acc[k];
             }
-        }
-        __syncthreads();
-
-        // bhat_e = rho_e + kappa H_eo t_o ; r = bhat_e ; x = 0
-        cpx<R> r[12], x[12], p[12];
-        B.inner_hops(se, nbe, sT, Vh, acc);
-#pragma unroll
-        for (int k = 0; k < 12; k++) {
-            r[k] = re[k] + kappa * acc[k];
-            x[k] = mk<R>(0, 0);
-            sR[k * Vh + i] = r[k];
-        }
-        __syncthreads();
-
-        for (int it = 0; it < a.nmr; it++) {
-            // t_o = A_oo^{-1} (-kappa H_oe r)
-            {
-                cpx<R> u[12], t[12];
-                B.inner_hops(so, nbo, sR, 0, acc);
-#pragma unroll
-                for (int k = 0; k < 12; k++) u[k] = (-kappa) * acc[k];
-                B.clover(so, u, t);
-#pragma unroll
-                for (int k = 0; k < 12; k++) sT[k * Vh + i] = t[k];
-            }
-            __syncthreads();
-            // p = A_ee r + kappa H_eo t_o ; dots
-            B.inner_hops(se, nbe, sT, Vh, acc);
-            B.clover(se, r, p);
-            R pr_re = 0, pr_im = 0, pp = 0;
-#pragma unroll
-            for (int k = 0; k < 12; k++) {
-                p[k] = p[k] + kappa * acc[k];
-                pr_re = fma(p[k].re, r[k].re, pr_re);
-                pr_re = fma(p[k].im, r[k].im, pr_re);
-                pr_im = fma(p[k].re, r[k].im, pr_im);
-                pr_im = fma(-p[k].im, r[k].re, pr_im);
-                pp = fma(p[k].re, p[k].re, pp);
-                pp = fma(p[k].im, p[k].im, pp);
-            }
-            if (full_warps) {
-                pr_re = warp_sum(pr_re);
-                pr_im = warp_sum(pr_im);
-                pp = warp_sum(pp);
-                if ((i & 31) == 0) {
-                    sRed[(i >> 5) * 4 + 0] = pr_re;
-                    sRed[(i >> 5) * 4 + 1] = pr_im;
-                    sRed[(i >> 5) * 4 + 2] = pp;
-                }
+            if (a.gather_only) {
+                store_sp<R, SS>(a.rho, rb, sb, d, s, Vd, v);
             } else {
-                // partial warp (Vh < 32): per-thread partials, summed in order below
-                sRed[i * 3 + 0] = pr_re;
-                sRed[i * 3 + 1] = pr_im;
-                sRed[i * 3 + 2] = pp;
+                cpx<R> *dst = par ? sRo : sR;  // rho_e parks in sR until the setup phase
+#pragma unroll
+                for (int k = 0; k < 12; k++) dst[k * Vh + i] = v[k];
             }
-            __syncthreads();
-            R tr = 0, ti_ = 0, tp = 0;
-            if (full_warps) {
-                for (int w = 0; w < nwarps; w++) {
-                    tr += sRed[w * 4 + 0];
-                    ti_ += sRed[w * 4 + 1];
-                    tp += sRed[w * 4 + 2];
-                }
+        }
+        if (a.gather_only) continue;
+
+        cpx<R> r[12], x[12];
+#pragma unroll
+        for (int k = 0; k < 12; k++) x[k] = mk<R>(0, 0);
+
+        for (int ph = 0; ph < nphase; ph++) {
+            const int type = ph == 0 ? PH_SETUP_ODD
+                             : ph == 1 ? PH_SETUP_EVEN
+                             : ph == nphase - 1 ? PH_RECON_ODD
+                             : ((ph & 1) ? PH_MR_EVEN : PH_MR_ODD);
+            const int par = (type == PH_SETUP_EVEN || type == PH_MR_EVEN) ? 0 : 1;
+            const int s = par ? so : se;
+
+            // hop sum from the other parity's half-field (Dirichlet boundary)
+            if (type != PH_SETUP_ODD) {
+                uint16_t nb[8];
+#pragma unroll
+                for (int k = 0; k < 8; k++) nb[k] = par ? nbo[k] : nbe[k];
+                B.inner_hops(s, nb, par ? sR : sT, par ? 0 : Vh, acc);
             } else {
-                for (int w = 0; w < Vh; w++) {
-                    tr += sRed[w * 3 + 0];
-                    ti_ += sRed[w * 3 + 1];
-                    tp += sRed[w * 3 + 2];
-                }
+#pragma unroll
+                for (int k = 0; k < 12; k++) acc[k] = mk<R>(0, 0);
             }
-            cpx<R> alpha = tp > (R)0 ? mk<R>(tr / tp, ti_ / tp) : mk<R>(0, 0);
-            const bool last = it == a.nmr - 1;
+
+            // own operand and clover input
+            //   setup-odd: A^-1 rho_o     mr-odd: A^-1 (-k acc)
+            //   mr-even:   A r            recon:  A^-1 (rho_o + k acc)
+            if (type == PH_SETUP_EVEN) {
+                // r = rho_e + kappa acc; with nmr = 0 the reconstruction reads x = 0
+#pragma unroll
+                for (int k = 0; k < 12; k++) {
+                    r[k] = sR[k * Vh + i] + kappa * acc[k];
+                    sR[k * Vh + i] = a.nmr > 0 ? r[k] : x[k];
+                }
+                __syncthreads();
+                continue;
+            }
 #pragma unroll
             for (int k = 0; k < 12; k++) {
-                cfma(x[k], alpha, r[k]);
-                r[k] = r[k] - alpha * p[k];
+                cpx<R> own = type == PH_MR_EVEN ? r[k] : (type == PH_MR_ODD ? mk<R>(0, 0) : sRo[k * Vh + i]);
+                R ka = type == PH_MR_EVEN || type == PH_SETUP_ODD ? (R)0 : (type == PH_MR_ODD ? -kappa : kappa);
+                v[k] = own + ka * acc[k];
             }
-            // sR was last read before the first barrier of this step, and sRed is
-            // rewritten only after the next step's first barrier
+            cpx<R> c[12];
+            B.clover(s, v, c);
+
+            if (type == PH_MR_EVEN) {
+                // p = A r + kappa acc ; alpha = <p,r>/<p,p> ; x += alpha r ; r -= alpha p
+                R pr_re = 0, pr_im = 0, pp = 0;
 #pragma unroll
-            for (int k = 0; k < 12; k++) sR[k * Vh + i] = last ? x[k] : r[k];
+                for (int k = 0; k < 12; k++) {
+                    c[k] = c[k] + kappa * acc[k];
+                    pr_re = fma(c[k].re, r[k].re, pr_re);
+                    pr_re = fma(c[k].im, r[k].im, pr_re);
+                    pr_im = fma(c[k].re, r[k].im, pr_im);
+                    pr_im = fma(-c[k].im, r[k].re, pr_im);
+                    pp = fma(c[k].re, c[k].re, pp);
+                    pp = fma(c[k].im, c[k].im, pp);
+                }
+                if (full_warps) {
+                    pr_re = warp_sum(pr_re);
+                    pr_im = warp_sum(pr_im);
+                    pp = warp_sum(pp);
+                    if ((i & 31) == 0) {
+                        sRed[(i >> 5) * 4 + 0] = pr_re;
+                        sRed[(i >> 5) * 4 + 1] = pr_im;
+                        sRed[(i >> 5) * 4 + 2] = pp;
+                    }
+                } else {
+                    // partial warp (Vh < 32): per-thread partials, summed in order below
+                    sRed[i * 3 + 0] = pr_re;
+                    sRed[i * 3 + 1] = pr_im;
+                    sRed[i * 3 + 2] = pp;
+                }
+                __syncthreads();
+                R tr = 0, ti_ = 0, tp = 0;
+                if (full_warps) {
+                    for (int w = 0; w < nwarps; w++) {
+                        tr += sRed[w * 4 + 0];
+                        ti_ += sRed[w * 4 + 1];
+                        tp += sRed[w * 4 + 2];
+                    }
+                } else {
+                    for (int w = 0; w < Vh; w++) {
+                        tr += sRed[w * 3 + 0];
+                        ti_ += sRed[w * 3 + 1];
+                        tp += sRed[w * 3 + 2];
+                    }
+                }
+                cpx<R> alpha = tp > (R)0 ? mk<R>(tr / tp, ti_ / tp) : mk<R>(0, 0);
+                const bool last = ph == nphase - 2;
+                // sR was last read before this phase's hop sum completed on
+                // every thread (barrier above); sRed is rewritten only after
+                // the next phase's barrier
+#pragma unroll
+                for (int k = 0; k < 12; k++) {
+                    cfma(x[k], alpha, r[k]);
+                    r[k] = r[k] - alpha * c[k];
+                    sR[k * Vh + i] = last ? x[k] : r[k];
+                }
+            } else if (type == PH_RECON_ODD) {
+                // outputs: delta, psi, rho on this domain
+                store_sp<R, SS>(a.delta, rb, sb, d, se, Vd, x);
+                store_sp<R, SS>(a.delta, rb, sb, d, so, Vd, c);
+                if (a.first_psi) {
+                    store_sp<R, SP>(a.psi, rb, sb, d, se, Vd, x);
+                    store_sp<R, SP>(a.psi, rb, sb, d, so, Vd, c);
+                } else {
+                    cpx<R> q[12];
+                    load_sp<R, SP>(a.psi, rb, sb, d, se, Vd, q);
+#pragma unroll
+                    for (int k = 0; k < 12; k++) q[k] = q[k] + x[k];
+                    store_sp<R, SP>(a.psi, rb, sb, d, se, Vd, q);
+                    load_sp<R, SP>(a.psi, rb, sb, d, so, Vd, q);
+#pragma unroll
+                    for (int k = 0; k < 12; k++) q[k] = q[k] + c[k];
+                    store_sp<R, SP>(a.psi, rb, sb, d, so, Vd, q);
+                }
+                store_sp<R, SS>(a.rho, rb, sb, d, se, Vd, r);
+#pragma unroll
+                for (int k = 0; k < 12; k++) c[k] = mk<R>(0, 0);
+                store_sp<R, SS>(a.rho, rb, sb, d, so, Vd, c);
+            } else {
+                // setup-odd / mr-odd: t_o -> sT
+#pragma unroll
+                for (int k = 0; k < 12; k++) sT[k * Vh + i] = c[k];
+            }
             __syncthreads();
         }
-        if (a.nmr == 0) {
-#pragma unroll
-            for (int k = 0; k < 12; k++) sR[k * Vh + i] = x[k];
-            __syncthreads();
-        }
-
-        // x_o = A_oo^{-1} (rho_o + kappa H_oe x_e)
-        cpx<R> xo[12];
-        {
-            cpx<R> u[12];
-            B.inner_hops(so, nbo, sR, 0, acc);
-#pragma unroll
-            for (int k = 0; k < 12; k++) u[k] = sRo[k * Vh + i] + kappa * acc[k];
-            B.clover(so, u, xo);
-        }
-
-        // outputs: delta, psi, rho on this domain
-        store_sp<R, SS>(a.delta, rb, sb, d, se, Vd, x);
-        store_sp<R, SS>(a.delta, rb, sb, d, so, Vd, xo);
-        if (a.first_psi) {
-            store_sp<R, SP>(a.psi, rb, sb, d, se, Vd, x);
-            store_sp<R, SP>(a.psi, rb, sb, d, so, Vd, xo);
-        } else {
-            cpx<R> q[12];
-            load_sp<R, SP>(a.psi, rb, sb, d, se, Vd, q);
-#pragma unroll
-            for (int k = 0; k < 12; k++) q[k] = q[k] + x[k];
-            store_sp<R, SP>(a.psi, rb, sb, d, se, Vd, q);
-            load_sp<R, SP>(a.psi, rb, sb, d, so, Vd, q);
-#pragma unroll
-            for (int k = 0; k < 12; k++) q[k] = q[k] + xo[k];
-            store_sp<R, SP>(a.psi, rb, sb, d, so, Vd, q);
-        }
-        store_sp<R, SS>(a.rho, rb, sb, d, se, Vd, r);
-#pragma unroll
-        for (int k = 0; k < 12; k++) xo[k] = mk<R>(0, 0);
-        store_sp<R, SS>(a.rho, rb, sb, d, so, Vd, xo);
-        __syncthreads();  // shared buffers are reused by the next right-hand side
     }
 }
 

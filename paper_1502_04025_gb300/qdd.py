@@ -158,8 +158,14 @@ def qdd_last_error() -> str:
     return _lib.qdd_last_error().decode(errors="replace")
 
 
-def qdd_set_profiling(ctx, on: bool):
-    _check(_lib.qdd_set_profiling(ctx, 1 if on else 0), "qdd_set_profiling")
+QDD_PROF_SAP, QDD_PROF_DSLASH, QDD_PROF_BLAS, QDD_PROF_OTHER, QDD_PROF_ALL = 1, 2, 4, 8, 15
+
+
+def qdd_set_profiling(ctx, classes=QDD_PROF_ALL):
+    """Event-time the selected kernel classes (bit mask; True = all, False/0 = off)."""
+    if classes is True:
+        classes = QDD_PROF_ALL
+    _check(_lib.qdd_set_profiling(ctx, int(classes)), "qdd_set_profiling")
 
 
 def qdd_get_kernel_times(ctx, reset: bool = False) -> dict:
