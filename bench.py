@@ -35,19 +35,39 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 WL = dict(L=(16, 16, 16, 32), dom=(8, 4, 4, 4), eps=0.5, csw=1.0, kappa=0.125, gauge_seed=1002, source_seed=2002,
-          nmr=4, ncy=4, m=16, tol=1e-10, sap_prec="f32", arnoldi_prec="f64")
+          nmr=4, ncy=4, m=16, tol=1e-10, sap_prec="f32", arnoldi_prec="df64")
 # full-lattice operator throughput: a lattice larger than L2 (32^3x64, eps 0.7, c_sw 1.5, kappa 0.1355)
 DSL = dict(L=(32, 32, 32, 64), dom=(4, 4, 4, 4), eps=0.7, csw=1.5, kappa=0.1355, gauge_seed=1003, source_seed=2003)
 METRIC = "SAP-FGMRES time-to-1e-10 residual"
 WORKLOAD_NAME = ("16^3x32 Wilson-clover, c_sw 1.0, kappa 0.125, eps 0.5 links; SAP-FGMRES(16), 8x4x4x4 domains, "
-                 "nmr 4, ncy 4, FP32 preconditioner, FP64 outer, tol 1e-10, 1 Gaussian source")
+                 "nmr 4, ncy 4, FP32 preconditioner, FP64 outer (double-float Arnoldi operator), tol 1e-10, "
+                 "1 Gaussian source")
 SAP_FLOP = {"hop": 1320, "clover": 504, "combine": 24, "mr_blas": 336, "boundary_hop": 168}
 L2_FLUSH_BYTES = 256 << 20
+
+
+# the other workload configurations (run with --config N; the default line is configuration 2)
+CONFIGS = {
+    1: dict(L=(8, 8, 8, 8), dom=(4, 4, 4, 4), eps=0.5, csw=1.0, kappa=0.12, gauge_seed=1001, source_seed=2001,
+            nmr=4, ncy=4, m=16, tol=1e-10, sap_prec="f64", arnoldi_prec="f64", source="gaussian", nrhs=1,
+            name="8^4 plain FP64 SAP-FGMRES(16), 4^4 domains, c_sw 1.0, kappa 0.12, eps 0.5"),
+    2: dict(WL, source="gaussian", nrhs=1, name=WORKLOAD_NAME),
+    3: dict(L=(32, 32, 32, 64), dom=(4, 4, 4, 4), eps=0.7, csw=1.5, kappa=0.1355, gauge_seed=1003, source_seed=2003,
+            nmr=4, ncy=4, m=16, tol=1e-10, sap_prec="f16", arnoldi_prec="df64", source="point12", nrhs=12,
+            name="32^3x64, eps 0.7, c_sw 1.5, kappa 0.1355, FP16-stored SAP, FP64 outer, 12 point sources batched"),
+    4: dict(L=(48, 48, 48, 96), dom=(4, 4, 4, 4), eps=0.7, csw=1.5, kappa=0.1355, gauge_seed=1004, source_seed=2004,
+            nmr=4, ncy=4, m=16, tol=1e-10, sap_prec="bf16", arnoldi_prec="df64", source="z2", nrhs=1,
+            name="48^3x96, eps 0.7, c_sw 1.5, kappa 0.1355, BF16-stored SAP, FP64 FGMRES(16), Z2 source"),
+}
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4],
+                    help="workload configuration (2 = the default benchmark line)")
+    ap.add_argument("--serve", action="store_true", help="run the serving mix instead of single solves")
+    ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["qdd", "reference"], default="qdd")
@@ -192,6 +212,33 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ GPU leg
 
+def make_sources(W):
+    from paper_1502_04025_gb300 import inputs
+
+    if W["source"] == "point12":
+        return np.ascontiguousarray(inputs.point_sources(W["L"]))
+    if W["source"] == "z2":
+        return inputs.z2_source(W["L"], W["source_seed"])
+    return inputs.gaussian_source(W["L"], W["source_seed"])
+
+
+def sampled_residual(W, U, b, x, nsites=64, seed=7):
+    """True residual of the returned solution at sampled sites, from the FP64
+    oracle (max over right-hand sides of |b - D x|_S / |b|)."""
+    from oracle import pyoracle as ora
+
+    V = int(np.prod(W["L"]))
+    sites = np.random.Generator(np.random.Philox(seed)).choice(V, size=min(nsites, V), replace=False)
+    bs = b.reshape(-1, V, 4, 3)
+    xs = x.reshape(-1, V, 4, 3)
+    worst = 0.0
+    for r in range(bs.shape[0]):
+        dx = ora.apply_D_sites(W["L"], U, W["csw"], W["kappa"], xs[r], sites)
+        res = np.linalg.norm(bs[r][sites] - dx) / np.linalg.norm(bs[r])
+        worst = max(worst, float(res))
+    return {"sites": int(len(sites)), "max_rel_residual_at_sites": worst}
+
+
 def run_qdd(args):
     import torch
 
@@ -215,14 +262,17 @@ def run_qdd(args):
     build.build()
     from paper_1502_04025_gb300 import qdd
 
+    W = CONFIGS[args.config]
     pk, pk_kind = peaks()
     ctx = qdd.qdd_create(local, 0)
-    U = inputs.gauge_field(WL["L"], WL["eps"], WL["gauge_seed"])
-    b = inputs.gaussian_source(WL["L"], WL["source_seed"])
-    g = qdd.qdd_create_gauge_field(ctx, WL["L"], WL["dom"], U)
-    qdd.qdd_set_clover(g, WL["csw"], WL["kappa"])
-    params = qdd.qdd_default_params(tol=WL["tol"], restart_m=WL["m"], nmr=WL["nmr"], ncy=WL["ncy"],
-                                    sap_prec=WL["sap_prec"], arnoldi_prec=WL["arnoldi_prec"], max_restarts=50)
+    U = inputs.gauge_field(W["L"], W["eps"], W["gauge_seed"])
+    b = make_sources(W)
+    nrhs = W["nrhs"]
+    g = qdd.qdd_create_gauge_field(ctx, W["L"], W["dom"], U)
+    qdd.qdd_set_clover(g, W["csw"], W["kappa"])
+    params = qdd.qdd_default_params(tol=W["tol"], restart_m=W["m"], nmr=W["nmr"], ncy=W["ncy"],
+                                    sap_prec=W["sap_prec"], arnoldi_prec=W["arnoldi_prec"], max_restarts=200,
+                                    nrhs=nrhs)
     bd = torch.from_numpy(b).cuda()
     xd = torch.empty_like(bd)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -236,7 +286,7 @@ def run_qdd(args):
     clocks.start()  # the clock sampler starts during warm-up, before the timed region
     for _ in range(args.warmup):
         flush.fill_(1.0)
-        _, rep = qdd.qdd_solve(g, bd, params, x=xd)
+        _, rep = qdd.qdd_solve(g, bd, params, x=xd, allow_noconv=True)
     torch.cuda.synchronize()
 
     # ---- timed region: K solves, inputs resident, L2 flushed before each
@@ -247,7 +297,7 @@ def run_qdd(args):
     reps = []
     for _ in range(args.steps):
         flush.fill_(1.0)
-        _, rep = qdd.qdd_solve(g, bd, params, x=xd)
+        _, rep = qdd.qdd_solve(g, bd, params, x=xd, allow_noconv=True)
         reps.append(rep)
     e1.record(stream)
     barrier()
@@ -266,32 +316,32 @@ def run_qdd(args):
     qdd.qdd_set_profiling(ctx, qdd.QDD_PROF_ALL)
     qdd.qdd_get_kernel_times(ctx, reset=True)
     flush.fill_(1.0)
-    qdd.qdd_solve(g, bd, params, x=xd)
+    qdd.qdd_solve(g, bd, params, x=xd, allow_noconv=True)
     shares = qdd.qdd_get_kernel_times(ctx, reset=True)
     qdd.qdd_set_profiling(ctx, 0)
 
     # ---- roofline of the dominant kernel class (timed inside the timed region)
     classes = {k: v for k, v in shares.items() if v[1] > 0}
     dom_cls = max(classes, key=lambda k: classes[k][0])
-    V = int(np.prod(WL["L"]))
-    Vd = int(np.prod(WL["dom"]))
+    V = int(np.prod(W["L"]))
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
     fp32_peak = sm_count * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12  # TFLOP/s
-    # per-launch time from the timed region when that class was event-timed there
     kt = kt if kt[dom_cls][0] > 0 else shares
     if dom_cls == "sap":
         ms_launch = kt["sap"][0] / kt["sap"][1]
-        flop = (V // 2) * sap_flop_per_site(WL["dom"], WL["nmr"])
+        flop = nrhs * (V // 2) * sap_flop_per_site(W["dom"], W["nmr"])
         achieved = flop / (ms_launch * 1e-3) / 1e12
-        roof = {"kernel": "k_sap (Schwarz colour half-sweep, FP32)", "bound": "alu", "achieved": achieved,
-                "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
-                "ms_per_launch": ms_launch, "launches": kt["sap"][1],
+        roof = {"kernel": f"k_sap (Schwarz colour half-sweep, {W['sap_prec']} storage, FP32 arithmetic)"
+                if W["sap_prec"] != "f64" else "k_sap (Schwarz colour half-sweep, FP64)",
+                "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": None, "ms_per_launch": ms_launch, "launches": kt["sap"][1],
+                "flop_per_launch": flop,
                 "peak_source": f"{sm_count} SMs x 128 FP32 lanes x 2 flop x {pk.get('sm_max_mhz', 2070.0):.0f} MHz"}
     elif dom_cls == "dslash":
         ms_launch = kt["dslash"][0] / kt["dslash"][1]
-        bytes_site = 576 + 576 + 96 + 192  # FP64 links + clover, FP32 input, FP64 output
-        achieved = V * bytes_site / (ms_launch * 1e-3) / 1e9
-        roof = {"kernel": "k_dslash (FP64 operator in the Arnoldi step)", "bound": "hbm", "achieved": achieved,
+        bytes_site = 576 + 576 + 96 + 192  # FP64-width links + clover, FP32 input, FP64 output
+        achieved = nrhs * V * bytes_site / (ms_launch * 1e-3) / 1e9
+        roof = {"kernel": "k_dslash (operator in the Arnoldi step)", "bound": "hbm", "achieved": achieved,
                 "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": None,
                 "ms_per_launch": ms_launch, "launches": kt["dslash"][1]}
     else:
@@ -309,16 +359,20 @@ def run_qdd(args):
         flush.fill_(1.0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        _, r2 = qdd.qdd_solve(g, b, params, x=xh)
+        _, r2 = qdd.qdd_solve(g, b, params, x=xh, allow_noconv=True)
         t1 = time.perf_counter()
         if k > 0:
             e2e_ms.append((t1 - t0) * 1e3)
     e2e = {"value": statistics.mean(e2e_ms) if e2e_ms else None, "unit": "ms",
            "h2d_bytes_per_step": int(b.nbytes), "d2h_bytes_per_step": int(xh.nbytes)}
+    parity = None
+    if rank == 0 and args.config != 2 and e2e_ms:
+        parity = sampled_residual(W, U, b, xh)
 
     # ---- full-lattice operator throughput (FP32 and FP16 storage) on a lattice > L2
     dslash = None
-    if not args.no_dslash and rank == 0:
+    if not args.no_dslash and rank == 0 and args.config == 2:
+        del U
         Ud = inputs.gauge_field(DSL["L"], DSL["eps"], DSL["gauge_seed"])
         gd = qdd.qdd_create_gauge_field(ctx, DSL["L"], DSL["dom"], Ud)
         del Ud
@@ -327,7 +381,7 @@ def run_qdd(args):
         ys = torch.empty_like(xs)
         Vl = int(np.prod(DSL["L"]))
         dslash = {"lattice": list(DSL["L"]), "flop_per_site": 1848}
-        for prec, bps in (("f32", 768), ("f16", 392), ("f64", 1536)):
+        for prec, bps in (("f32", 768), ("f16", 392), ("df64", 1536), ("f64", 1536)):
             for _ in range(3):
                 qdd.qdd_apply_D(gd, xs, prec, out=ys)
             qdd.qdd_set_profiling(ctx, qdd.QDD_PROF_DSLASH)
@@ -342,9 +396,10 @@ def run_qdd(args):
                             "frac_hbm": bps * Vl / (ms * 1e-3) / 1e9 / pk["hbm_gbs"],
                             "bytes_per_site": bps}
         qdd.qdd_destroy_gauge(gd)
+        U = None
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.config == 2:
         try:
             cpu = oracle_sample(WL, U)
         except Exception as e:  # the GPU number stands without it
@@ -354,15 +409,22 @@ def run_qdd(args):
         last = reps[-1]
         line = {"metric": METRIC, "value": ms_step, "unit": "ms", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64 outer / f32 preconditioner", "data": "synthetic",
-                "config": {"workload": WORKLOAD_NAME, "lattice": list(WL["L"]), "domain": list(WL["dom"]),
-                           "kappa": WL["kappa"], "c_sw": WL["csw"], "eps": WL["eps"], "nmr": WL["nmr"],
-                           "ncy": WL["ncy"], "restart_m": WL["m"], "tol": WL["tol"],
-                           "l2": "256 MB buffer written before every step; Krylov working set 0.7 GB",
+                "vs_baseline": None,
+                "dtype": ("f64" if W["sap_prec"] == "f64" else f"f64 outer / f32 arithmetic on {W['sap_prec']} "
+                          "preconditioner storage"),
+                "data": "synthetic",
+                "config": {"workload": W["name"], "config": args.config, "lattice": list(W["L"]),
+                           "domain": list(W["dom"]), "kappa": W["kappa"], "c_sw": W["csw"], "eps": W["eps"],
+                           "nmr": W["nmr"], "ncy": W["ncy"], "restart_m": W["m"], "tol": W["tol"], "nrhs": nrhs,
+                           "sap_prec": W["sap_prec"], "arnoldi_prec": W["arnoldi_prec"],
+                           "l2": "256 MB buffer written before every step; Krylov working set larger than L2",
                            "parallelism": f"{world} replica(s)"},
                 "iters": last["iters"], "restarts": last["restarts"], "true_rel_res": last["true_rel_res"],
+                "converged": bool(last["converged"]),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
                 "dslash": dslash}
+        if parity is not None:
+            line["parity"] = parity
         print(json.dumps(line), flush=True)
     qdd.qdd_destroy_gauge(g)
     qdd.qdd_destroy(ctx)
@@ -370,10 +432,99 @@ def run_qdd(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------- serving
+
+SERVE_LATTICES = [((8, 8, 8, 8), (4, 4, 4, 4)), ((16, 16, 16, 32), (8, 4, 4, 4)),
+                  ((24, 24, 24, 48), (4, 4, 4, 4)), ((32, 32, 32, 64), (4, 4, 4, 4))]
+SERVE_KAPPAS = [0.120, 0.125, 0.130, 0.135]
+
+
+def run_serve(args):
+    """Poisson arrivals of solves on four lattice sizes with kappa in
+    [0.120, 0.135] (four resident values) and 1-12 right-hand sides, FP32
+    preconditioner, double-float Arnoldi operator, tol 1e-10, admission by an
+    80% HBM budget; reports p50/p99 latency (submit to result) and solves/s."""
+    import torch
+
+    from paper_1502_04025_gb300 import build, inputs
+
+    build.build()
+    from paper_1502_04025_gb300 import qdd
+
+    ctx = qdd.qdd_create(0, 0)
+    qdd.qdd_serve_config(ctx, 4)
+    gauges = {}
+    for li, (L, dom) in enumerate(SERVE_LATTICES):
+        U = inputs.gauge_field(L, 0.5, 1100 + li)
+        for ki, k in enumerate(SERVE_KAPPAS):
+            g = qdd.qdd_create_gauge_field(ctx, L, dom, U)
+            qdd.qdd_set_clover(g, 1.0, k)
+            gauges[(li, ki)] = g
+        del U
+    rng = np.random.Generator(np.random.Philox(3001))
+    n = args.serve_requests
+    reqs = []
+    for i in range(n):
+        li = int(rng.integers(0, len(SERVE_LATTICES)))
+        ki = int(rng.integers(0, len(SERVE_KAPPAS)))
+        nrhs = int(rng.integers(1, 13))
+        reqs.append((li, ki, nrhs))
+    params = {r: qdd.qdd_default_params(tol=1e-10, sap_prec="f32", arnoldi_prec="df64", nrhs=r, max_restarts=200)
+              for r in range(1, 13)}
+    srcs = {}
+    for li, (L, dom) in enumerate(SERVE_LATTICES):
+        srcs[li] = inputs.gaussian_source(L, 3100 + li, nrhs=12).reshape(12, -1, 4, 3)
+    # calibrate: solve time of one request of each lattice with 1 and 12 rhs
+    cal = {}
+    for li in range(len(SERVE_LATTICES)):
+        for r in (1, 12):
+            bb = np.ascontiguousarray(srcs[li][:r])
+            t0 = time.perf_counter()
+            qdd.qdd_solve(gauges[(li, 0)], bb if r > 1 else np.ascontiguousarray(bb[0]), params[r])
+            cal[(li, r)] = time.perf_counter() - t0
+    mean_service = np.mean([cal[(li, 1)] + (cal[(li, 12)] - cal[(li, 1)]) * (r - 1) / 11 for li, _, r in reqs])
+    rate = 0.7 / mean_service  # requests per second for ~70% busy
+    gaps = rng.exponential(1.0 / rate, size=n)
+    tickets = []
+    t_start = time.perf_counter()
+    t_next = t_start
+    xs = []
+    for i, (li, ki, r) in enumerate(reqs):
+        t_next += gaps[i]
+        while time.perf_counter() < t_next:
+            time.sleep(max(0.0, min(0.001, t_next - time.perf_counter())))
+        bb = np.ascontiguousarray(srcs[li][:r]) if r > 1 else np.ascontiguousarray(srcs[li][0])
+        x = np.zeros_like(bb)
+        xs.append(x)
+        tickets.append((qdd.qdd_submit(ctx, gauges[(li, ki)], bb, x, params[r]), time.perf_counter()))
+    lat, ok = [], 0
+    for t, ts in tickets:
+        st, rep = qdd.qdd_poll(ctx, t, 600.0)
+        if st == qdd.QDD_OK and rep["converged"]:
+            ok += 1
+            lat.append(rep["seconds"])
+    wall = time.perf_counter() - t_start
+    used, budget = qdd.qdd_memory(ctx)
+    line = {"metric": "SAP-FGMRES serving latency (submit to result)", "value": float(np.percentile(lat, 50)) * 1e3,
+            "unit": "ms", "higher_is_better": False, "p50_ms": float(np.percentile(lat, 50)) * 1e3,
+            "p99_ms": float(np.percentile(lat, 99)) * 1e3, "solves_per_s": ok / wall, "requests": n,
+            "converged": ok, "offered_rate_per_s": rate, "wall_s": wall, "data": "synthetic",
+            "config": {"workload": "serving mix: Poisson arrivals, lattices 8^4/16^3x32/24^3x48/32^3x64, "
+                                   "kappa in {0.120,0.125,0.130,0.135}, 1-12 rhs, FP32 SAP, tol 1e-10",
+                       "slots": 4, "hbm_budget_bytes": budget, "resident_gauge_bytes": used},
+            "calibration_s": {f"{SERVE_LATTICES[li][0]}x{r}": v for (li, r), v in cal.items()}}
+    print(json.dumps(line), flush=True)
+    for g in gauges.values():
+        qdd.qdd_destroy_gauge(g)
+    qdd.qdd_destroy(ctx)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.serve:
+        run_serve(args)
     else:
         run_qdd(args)
 

@@ -66,7 +66,10 @@ typedef enum {
     QDD_PREC_F64 = 0,
     QDD_PREC_F32 = 1,
     QDD_PREC_F16S = 2,
-    QDD_PREC_BF16S = 3
+    QDD_PREC_BF16S = 3,
+    QDD_PREC_DF64 = 4 /* operator only: FP64-class accuracy (about 2^-46) from
+                         pairs of FP32 numbers; links and clover split into
+                         hi + lo parts.  For qdd_apply_D and arnoldi_prec. */
 } qdd_prec;
 
 typedef struct {
@@ -76,7 +79,8 @@ typedef struct {
     int nmr;              /* MR steps per domain visit */
     int ncy;              /* Schwarz cycles per preconditioner application */
     qdd_prec sap_prec;    /* preconditioner precision */
-    qdd_prec arnoldi_prec;/* QDD_PREC_F64 or QDD_PREC_F32: operator in w = D z_j */
+    qdd_prec arnoldi_prec;/* QDD_PREC_F64, QDD_PREC_DF64 or QDD_PREC_F32: operator
+                             in w = D z_j (the restart residual is always FP64) */
     int use_sap;          /* 0: no preconditioner (plain GMRES) */
     int nrhs;             /* right-hand sides solved together (1..12) */
     int reorth;           /* Gram-Schmidt: 0 classical, 1 classical with
@@ -168,7 +172,8 @@ qdd_status qdd_get_clover(qdd_gauge *g, int which, double *out);
 
 /*
  * out = D in for nrhs spinors (host layout), periodic boundary conditions.
- * prec = QDD_PREC_F64 computes in FP64; QDD_PREC_F32 converts links, clover
+ * prec = QDD_PREC_F64 computes in FP64; QDD_PREC_DF64 in double-float
+ * (FP32 pairs, about 2^-46 relative); QDD_PREC_F32 converts links, clover
  * and input to FP32 and computes in FP32 (1848 flop per site); F16S / BF16S
  * read 16-bit links/clover/spinor with FP32 arithmetic.
  */

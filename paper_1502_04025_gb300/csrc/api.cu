@@ -129,6 +129,7 @@ static size_t elem_bytes(qdd_prec p)
 {
     switch (p) {
     case QDD_PREC_F64: return 16;
+    case QDD_PREC_DF64: return 16;
     case QDD_PREC_F32: return 8;
     default: return 4;
     }
@@ -137,7 +138,7 @@ static size_t elem_bytes(qdd_prec p)
 qdd_status ensure_copy(Gauge *g, qdd_prec prec, cudaStream_t s)
 {
     if (prec == QDD_PREC_F64) return QDD_OK;
-    if (prec < QDD_PREC_F64 || prec > QDD_PREC_BF16S) {
+    if (prec < QDD_PREC_F64 || prec > QDD_PREC_DF64) {
         set_error("invalid precision %d", (int)prec);
         return QDD_EINVAL;
     }
@@ -147,6 +148,16 @@ qdd_status ensure_copy(Gauge *g, qdd_prec prec, cudaStream_t s)
     if (!g->have_clover) {
         set_error("set_clover has not been called");
         return QDD_EINVAL;
+    }
+    if (prec == QDD_PREC_DF64) {
+        // links and clover split into hi + lo FP32 parts (the operator only)
+        const size_t n = (size_t)g->hg.V * 36;
+        QDD_TRY(c.links.ensure(g->ctx, n * sizeof(float4)));
+        QDD_TRY(c.clov.ensure(g->ctx, n * sizeof(float4)));
+        QDD_TRY(launch_split_convert(g, g->links64.as<double2>(), c.links.as<float4>(), (int64_t)n, s));
+        QDD_TRY(launch_split_convert(g, g->clov64.as<double2>(), c.clov.as<float4>(), (int64_t)n, s));
+        c.valid = true;
+        return QDD_OK;
     }
     const size_t V = g->hg.V, eb = elem_bytes(prec);
     const bool scaled = prec == QDD_PREC_F16S || prec == QDD_PREC_BF16S;
@@ -364,7 +375,7 @@ qdd_status qdd_set_clover(qdd_gauge *g, double c_sw, double kappa)
     int singular = 0;
     QDD_CUDA(cudaMemcpy(&singular, flag.p, sizeof(int), cudaMemcpyDeviceToHost));
     g->ctx->timer.resolve();
-    for (int p = 0; p < 4; p++) g->copies[p].valid = false;
+    for (int p = 0; p < 5; p++) g->copies[p].valid = false;
     g->have_clover = false;
     if (singular) {
         set_error("clover block singular on %d sites", singular);
@@ -420,7 +431,7 @@ qdd_status qdd_apply_D(qdd_gauge *g, const double *in, double *out, int nrhs, qd
                        void *stream)
 {
     clear_error();
-    if (!g || !in || !out || nrhs < 1 || prec < QDD_PREC_F64 || prec > QDD_PREC_BF16S) {
+    if (!g || !in || !out || nrhs < 1 || prec < QDD_PREC_F64 || prec > QDD_PREC_DF64) {
         set_error("invalid argument");
         return QDD_EINVAL;
     }
@@ -433,6 +444,9 @@ qdd_status qdd_apply_D(qdd_gauge *g, const double *in, double *out, int nrhs, qd
     const size_t V = g->hg.V;
     const size_t eb = elem_bytes(prec);
     const bool scaled = prec == QDD_PREC_F16S || prec == QDD_PREC_BF16S;
+    const qdd_prec arith = prec == QDD_PREC_F64 || prec == QDD_PREC_DF64 ? prec : QDD_PREC_F32;
+    const qdd_prec fp = prec;                                             // link / clover copy
+    if (prec == QDD_PREC_DF64) prec = QDD_PREC_F64;                       // spinor storage
     const double *din = nullptr;
     double *dout = nullptr;
     QDD_TRY(stage_in(g, st->io, in, nrhs, on_device, s, &din));
@@ -443,8 +457,7 @@ qdd_status qdd_apply_D(qdd_gauge *g, const double *in, double *out, int nrhs, qd
         QDD_TRY(st->b_s.ensure(g->ctx, V * 4 * nrhs));
     }
     QDD_TRY(launch_spinor_in(g, din, st->a.p, st->a_s.as<float>(), prec, nrhs, s));
-    qdd_prec arith = prec == QDD_PREC_F64 ? QDD_PREC_F64 : QDD_PREC_F32;
-    QDD_TRY(launch_dslash(g, arith, prec, st->a.p, st->a_s.as<float>(), prec, st->b.p, st->b_s.as<float>(), prec,
+    QDD_TRY(launch_dslash(g, arith, fp, st->a.p, st->a_s.as<float>(), prec, st->b.p, st->b_s.as<float>(), prec,
                           nullptr, nrhs, s));
     QDD_TRY(stage_out(g, st->io, out, nrhs, on_device, s, &dout));
     QDD_TRY(launch_spinor_out(g, st->b.p, st->b_s.as<float>(), dout, prec, nrhs, s));

@@ -286,6 +286,116 @@ __device__ __forceinline__ void herm6_mul(const cpx<R> *blk, const cpx<R> *in, c
         }
 }
 
+// ------------------------------------------------------------ double-float
+//
+// A value hi + lo held in two FP32 numbers (|lo| <= ulp(hi)/2), for operator
+// applications that need FP64-class accuracy on a GPU whose FP64 pipe is far
+// slower than its FP32 pipe.  Built from error-free transformations (Knuth's
+// TwoSum, Dekker's FastTwoSum, and the FMA form of the exact product); the
+// intrinsics keep the compiler from contracting or reordering them.
+
+struct df {
+    float hi, lo;
+};
+
+__device__ __forceinline__ df df_two_sum(float a, float b)
+{
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+__device__ __forceinline__ df df_fast_two_sum(float a, float b)
+{
+    float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+// a + b for double-floats
+__device__ __forceinline__ df df_add(df a, df b)
+{
+    df s = df_two_sum(a.hi, b.hi);
+    float e = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+    return df_fast_two_sum(s.hi, e);
+}
+
+__device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
+
+// compensated accumulator: s collects the leading parts with TwoSum, c the
+// rounding errors and low-order terms; value = s + c
+struct dfacc {
+    float s, c;
+};
+
+__device__ __forceinline__ void dfacc_zero(dfacc &a) { a.s = 0.f; a.c = 0.f; }
+
+// acc += x * y (x, y double-floats; the lo*lo term, below 2^-46 relative, is dropped)
+__device__ __forceinline__ void dfacc_mul_add(dfacc &acc, df x, df y)
+{
+    float p = __fmul_rn(x.hi, y.hi);
+    float e = __fmaf_rn(x.hi, y.hi, -p);
+    e = __fmaf_rn(x.hi, y.lo, e);
+    e = __fmaf_rn(x.lo, y.hi, e);
+    df t = df_two_sum(acc.s, p);
+    acc.s = t.hi;
+    acc.c = __fadd_rn(acc.c, __fadd_rn(t.lo, e));
+}
+
+// acc += x
+__device__ __forceinline__ void dfacc_add(dfacc &acc, df x)
+{
+    df t = df_two_sum(acc.s, x.hi);
+    acc.s = t.hi;
+    acc.c = __fadd_rn(acc.c, __fadd_rn(t.lo, x.lo));
+}
+
+__device__ __forceinline__ df dfacc_value(const dfacc &a) { return df_fast_two_sum(a.s, a.c); }
+
+__device__ __forceinline__ df df_from_double(double v)
+{
+    float hi = __double2float_rn(v);
+    return {hi, __double2float_rn(v - (double)hi)};
+}
+
+__device__ __forceinline__ double df_to_double(df v) { return (double)v.hi + (double)v.lo; }
+
+// complex double-float
+struct cdf {
+    df re, im;
+};
+
+__device__ __forceinline__ cdf cdf_add(cdf a, cdf b) { return {df_add(a.re, b.re), df_add(a.im, b.im)}; }
+__device__ __forceinline__ cdf cdf_sub(cdf a, cdf b) { return {df_add(a.re, df_neg(b.re)), df_add(a.im, df_neg(b.im))}; }
+__device__ __forceinline__ cdf cdf_ti(cdf a) { return {df_neg(a.im), a.re}; }   // i * a
+__device__ __forceinline__ cdf cdf_tmi(cdf a) { return {a.im, df_neg(a.re)}; }  // -i * a
+__device__ __forceinline__ cdf cdf_neg(cdf a) { return {df_neg(a.re), df_neg(a.im)}; }
+
+struct cdfacc {
+    dfacc re, im;
+};
+
+__device__ __forceinline__ void cdfacc_zero(cdfacc &a) { dfacc_zero(a.re); dfacc_zero(a.im); }
+
+// acc += a * b (CONJ: conj(a) * b)
+template <bool CONJ>
+__device__ __forceinline__ void cdfacc_mul_add(cdfacc &acc, cdf a, cdf b)
+{
+    dfacc_mul_add(acc.re, a.re, b.re);
+    dfacc_mul_add(acc.re, CONJ ? a.im : df_neg(a.im), b.im);
+    dfacc_mul_add(acc.im, a.re, b.im);
+    dfacc_mul_add(acc.im, CONJ ? df_neg(a.im) : a.im, b.re);
+}
+
+__device__ __forceinline__ cdf cdfacc_value(const cdfacc &a) { return {dfacc_value(a.re), dfacc_value(a.im)}; }
+
+// Storage of a double-float complex number: (re.hi, re.lo, im.hi, im.lo).
+struct StDF {
+    using T2 = float4;
+    static constexpr bool kScaled = false;
+    static constexpr int kBytes = 16;
+};
+
 // Runtime-checked device error flags (bounded waits that ran out, etc.).
 constexpr int kErrMbarTimeout = 1;
 

@@ -163,7 +163,7 @@ struct Gauge {
     bool have_clover = false;
     double csw = 0, kappa = 0;
     DevMem clov64, sclov64;   // FP64 clover A and Schwarz form (A even, A^-1 odd)
-    PrecCopy copies[4];       // index = qdd_prec; F64 entry aliases the masters
+    PrecCopy copies[5];       // index = qdd_prec; F64 entry aliases the masters
     std::unique_ptr<Workspace> ws;  // workspace of the synchronous entry points
     std::mutex mu;            // one synchronous call at a time per gauge object
     std::mutex copy_mu;       // guards the lazily built precision copies
@@ -194,6 +194,8 @@ qdd_status launch_spinor_convert(Gauge *g, const void *src, const float *src_sca
 qdd_status launch_links_convert(Gauge *g, qdd_prec dp, void *dst, cudaStream_t s);
 qdd_status launch_clover_convert(Gauge *g, const double2 *src, qdd_prec dp, void *dst, float *dst_scale,
                                  cudaStream_t s);
+// FP64 complex -> double-float (hi, lo) pairs
+qdd_status launch_split_convert(Gauge *g, const double2 *src, float4 *dst, int64_t n, cudaStream_t s);
 
 // clover.cu
 qdd_status launch_clover_build(Gauge *g, double csw, double kappa, int *d_singular, cudaStream_t s);

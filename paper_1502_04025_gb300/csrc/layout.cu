@@ -242,6 +242,16 @@ __global__ void k_links_convert(int64_t n, const double2 *src, typename S::T2 *d
     st_c<double>(dst + i, mk(a.x, a.y));
 }
 
+// FP64 complex -> (re.hi, re.lo, im.hi, im.lo) FP32 split
+__global__ void k_split_convert(int64_t n, const double2 *src, float4 *dst)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double2 a = __ldg(src + i);
+    float rh = __double2float_rn(a.x), ih = __double2float_rn(a.y);
+    dst[i] = make_float4(rh, __double2float_rn(a.x - (double)rh), ih, __double2float_rn(a.y - (double)ih));
+}
+
 // clover blocks: 36 planes per site; 16-bit formats get one scale per site
 template <typename S>
 __global__ void k_clover_convert(Geom g, const double2 *src, Field<S> dst)
@@ -347,6 +357,14 @@ qdd_status launch_links_convert(Gauge *g, qdd_prec dp, void *dst, cudaStream_t s
         k_links_convert<S><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, g->links64.as<double2>(),
                                                                         (typename S::T2 *)dst);
     });
+    QDD_CUDA(cudaGetLastError());
+    return QDD_OK;
+}
+
+qdd_status launch_split_convert(Gauge *g, const double2 *src, float4 *dst, int64_t n, cudaStream_t s)
+{
+    LaunchScope ls(g->ctx->timer, K_OTHER, s);
+    k_split_convert<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, src, dst);
     QDD_CUDA(cudaGetLastError());
     return QDD_OK;
 }

@@ -118,7 +118,8 @@ qdd_status solve_impl(Gauge *g, Workspace *wsp, const double *b_in, double *x_ou
     const int m = p->restart_m, B = p->nrhs;
     if (m < 1 || m > 64 || B < 1 || B > 64 || !(p->tol > 0) || p->max_restarts < 0 || p->nmr < 0 || p->ncy < 1 ||
         p->sap_prec < QDD_PREC_F64 || p->sap_prec > QDD_PREC_BF16S ||
-        (p->arnoldi_prec != QDD_PREC_F64 && p->arnoldi_prec != QDD_PREC_F32) || p->reorth < 0 || p->reorth > 2) {
+        (p->arnoldi_prec != QDD_PREC_F64 && p->arnoldi_prec != QDD_PREC_F32 && p->arnoldi_prec != QDD_PREC_DF64) ||
+        p->reorth < 0 || p->reorth > 2) {
         set_error("invalid solve parameters");
         return QDD_EINVAL;
     }
@@ -135,7 +136,7 @@ qdd_status solve_impl(Gauge *g, Workspace *wsp, const double *b_in, double *x_ou
     Workspace &w = *wsp;
     QDD_TRY(ensure_ws(g, w, m, B, sp, p->use_sap != 0));
     if (p->use_sap) QDD_TRY(ensure_copy(g, sp, s));
-    if (p->arnoldi_prec == QDD_PREC_F32) QDD_TRY(ensure_copy(g, QDD_PREC_F32, s));
+    if (p->arnoldi_prec != QDD_PREC_F64) QDD_TRY(ensure_copy(g, p->arnoldi_prec, s));
     const int64_t n = (int64_t)g->hg.V * 12;
     const int64_t ldV = n * B;  // stride between basis vectors of one rhs
     double2 *V = w.V.as<double2>();
@@ -230,9 +231,9 @@ qdd_status solve_impl(Gauge *g, Workspace *wsp, const double *b_in, double *x_ou
                 QDD_TRY(launch_spinor_convert(g, vj, nullptr, QDD_PREC_F64, zj, nullptr, zp, B, s));
             }
             // w = D z_j
-            if (p->arnoldi_prec == QDD_PREC_F64)
-                QDD_TRY(launch_dslash(g, QDD_PREC_F64, QDD_PREC_F64, zj, nullptr, zp, wv, nullptr, QDD_PREC_F64,
-                                      nullptr, B, s));
+            if (p->arnoldi_prec == QDD_PREC_F64 || p->arnoldi_prec == QDD_PREC_DF64)
+                QDD_TRY(launch_dslash(g, p->arnoldi_prec, p->arnoldi_prec, zj, nullptr, zp, wv, nullptr,
+                                      QDD_PREC_F64, nullptr, B, s));
             else
                 QDD_TRY(launch_dslash(g, QDD_PREC_F32, QDD_PREC_F32, zj, nullptr, QDD_PREC_F32, wv, nullptr,
                                       QDD_PREC_F64, nullptr, B, s));

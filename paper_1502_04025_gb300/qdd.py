@@ -19,8 +19,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libqdd.so")
 
 QDD_OK, QDD_EINVAL, QDD_ENOMEM, QDD_EBUDGET, QDD_ENOCONV, QDD_ENAN, QDD_ETIMEOUT, QDD_ECUDA, QDD_ENOTREADY = range(9)
-QDD_PREC_F64, QDD_PREC_F32, QDD_PREC_F16S, QDD_PREC_BF16S = range(4)
-PRECS = {"f64": QDD_PREC_F64, "f32": QDD_PREC_F32, "f16": QDD_PREC_F16S, "bf16": QDD_PREC_BF16S}
+QDD_PREC_F64, QDD_PREC_F32, QDD_PREC_F16S, QDD_PREC_BF16S, QDD_PREC_DF64 = range(5)
+PRECS = {"f64": QDD_PREC_F64, "f32": QDD_PREC_F32, "f16": QDD_PREC_F16S, "bf16": QDD_PREC_BF16S,
+         "df64": QDD_PREC_DF64}
 STATUS_NAMES = ["QDD_OK", "QDD_EINVAL", "QDD_ENOMEM", "QDD_EBUDGET", "QDD_ENOCONV", "QDD_ENAN", "QDD_ETIMEOUT",
                 "QDD_ECUDA", "QDD_ENOTREADY"]
 

@@ -3,6 +3,7 @@ the same seeded inputs.
 
 Tolerances (relative, in the 2-norm over the whole output unless stated):
   FP64 arithmetic            1e-12  (rounding order only)
+  double-float (FP32 pairs)  1e-12  (links, clover, input split to 2x24 bits; ~2^-46 per operation)
   FP32 arithmetic            1e-5   (the operator-apply bound of the target)
   FP16 storage + FP32 arith  4e-3   (2^-11 per stored component, ~10 terms)
   BF16 storage + FP32 arith  3e-2   (2^-8 per stored component)
@@ -14,7 +15,7 @@ from paper_1502_04025_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": 1e-12, "f32": 1e-5, "f16": 4e-3, "bf16": 3e-2}
+TOL = {"f64": 1e-12, "df64": 1e-12, "f32": 1e-5, "f16": 4e-3, "bf16": 3e-2}
 
 
 def rel(a, b):
@@ -87,14 +88,14 @@ def test_clover_matches_oracle(q, ctx, ora, L, dom):
 
 
 @pytest.mark.parametrize("L,dom", GEOMS)
-@pytest.mark.parametrize("prec", ["f64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("prec", ["f64", "df64", "f32", "f16", "bf16"])
 def test_dslash_matches_oracle(q, ctx, ora, L, dom, prec):
     P = problem(q, ctx, ora, L, dom)
     x = inputs.gaussian_source(L, 2001)
     want = ora.apply_D(L, P.U, P.A, P.kappa, x)
     got = q.qdd_apply_D(P.g, x, prec)
     assert rel(got, want) <= TOL[prec]
-    if prec == "f64":
+    if prec in ("f64", "df64"):
         assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
 
 
@@ -159,13 +160,24 @@ def test_solve_config1_fp64(q, ctx, ora):
     assert abs(rep2["iters"] - info["iters"]) <= 2
 
 
-@pytest.mark.parametrize("prec,arn", [("f32", "f64"), ("f16", "f64"), ("bf16", "f64"), ("f32", "f32")])
+@pytest.mark.parametrize("prec,arn", [("f32", "f64"), ("f16", "f64"), ("bf16", "f64"), ("f32", "f32"),
+                                      ("f32", "df64"), ("f64", "df64")])
 def test_solve_mixed_precision(q, ctx, ora, prec, arn):
     P = problem(q, ctx, ora, (16, 8, 8, 8), (8, 4, 4, 4), kappa=0.125)
     b = inputs.gaussian_source(P.L, 2002)
     x, rep = q.qdd_solve(P.g, b, tol=1e-10, sap_prec=prec, arnoldi_prec=arn)
     assert rep["converged"]
     assert _true_rel(ora, P, x, b) <= 1e-10
+
+
+def test_solve_df64_arnoldi_same_iterations(q, ctx, ora):
+    """The double-float Arnoldi operator keeps the FP64 iteration count."""
+    P = problem(q, ctx, ora, (16, 8, 8, 8), (8, 4, 4, 4), kappa=0.125)
+    b = inputs.gaussian_source(P.L, 2012)
+    x1, r1 = q.qdd_solve(P.g, b, tol=1e-10, sap_prec="f32", arnoldi_prec="f64")
+    x2, r2 = q.qdd_solve(P.g, b, tol=1e-10, sap_prec="f32", arnoldi_prec="df64")
+    assert r1["iters"] == r2["iters"] and r1["restarts"] == r2["restarts"]
+    assert rel(x2, x1) <= 1e-9
 
 
 def test_solve_plain_gmres_and_multi_rhs(q, ctx, ora):
