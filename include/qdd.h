@@ -168,6 +168,11 @@ qdd_status qdd_set_clover(qdd_gauge *g, double c_sw, double kappa);
  */
 qdd_status qdd_get_clover(qdd_gauge *g, int which, double *out);
 
+/* Schwarz kernel variant of this gauge field (a tuning choice; results agree
+ * to rounding): 0 automatic, 1 one thread per even/odd site pair, 2 two
+ * threads per pair (FP32-arithmetic precisions only; FP64 always uses 1). */
+qdd_status qdd_set_sap_variant(qdd_gauge *g, int variant);
+
 /* ------------------------------------------------------------- operators */
 
 /*

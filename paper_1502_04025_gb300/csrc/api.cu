@@ -427,6 +427,17 @@ qdd_status qdd_get_clover(qdd_gauge *g, int which, double *out)
     return QDD_OK;
 }
 
+qdd_status qdd_set_sap_variant(qdd_gauge *g, int variant)
+{
+    clear_error();
+    if (!g || variant < 0 || variant > 2) {
+        set_error("invalid argument");
+        return QDD_EINVAL;
+    }
+    g->sap_variant = variant;
+    return QDD_OK;
+}
+
 qdd_status qdd_apply_D(qdd_gauge *g, const double *in, double *out, int nrhs, qdd_prec prec, int on_device,
                        void *stream)
 {

@@ -167,6 +167,7 @@ struct Gauge {
     std::unique_ptr<Workspace> ws;  // workspace of the synchronous entry points
     std::mutex mu;            // one synchronous call at a time per gauge object
     std::mutex copy_mu;       // guards the lazily built precision copies
+    int sap_variant = 0;      // Schwarz kernel: 0 automatic, 1 one thread per site pair, 2 two
     ~Gauge();
 };
 

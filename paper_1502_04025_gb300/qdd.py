@@ -65,6 +65,7 @@ _SIGS = {
     "qdd_destroy_gauge": (None, [_vp]),
     "qdd_set_clover": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double]),
     "qdd_get_clover": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
+    "qdd_set_sap_variant": (ctypes.c_int, [_vp, ctypes.c_int]),
     "qdd_apply_D": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp]),
     "qdd_sap_apply": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_int, _vp]),
@@ -202,6 +203,10 @@ def qdd_get_clover(g, V: int, which: int = 0) -> np.ndarray:
     out = np.zeros((V, 2, 6, 6), dtype=np.complex128)
     _check(_lib.qdd_get_clover(g, which, out.ctypes.data), "qdd_get_clover")
     return out
+
+
+def qdd_set_sap_variant(g, variant: int):
+    _check(_lib.qdd_set_sap_variant(g, int(variant)), "qdd_set_sap_variant")
 
 
 # --------------------------------------------------------------- operators

@@ -128,6 +128,25 @@ def test_sap_lowp_matches_oracle(q, ctx, ora, L, dom, prec):
     assert rel(psi, psi_o) <= {"f32": 2e-5, "f16": 1e-2, "bf16": 6e-2}[prec]
 
 
+@pytest.mark.parametrize("L,dom", [GEOMS[0], GEOMS[1], GEOMS[2], GEOMS[3]])
+def test_sap_kernel_variants_agree(q, ctx, ora, L, dom):
+    """One and two threads per even/odd site pair: same FP32 Schwarz result
+    (to rounding), both within the FP32 bound of the oracle."""
+    P = problem(q, ctx, ora, L, dom)
+    eta = inputs.gaussian_source(L, 3004, nrhs=2)
+    eta = np.ascontiguousarray(eta)
+    psi_o, _ = ora.sap(L, dom, P.U, P.A, P.Ainv, P.kappa, eta[1], 4, 8)
+    out = {}
+    for variant in (1, 2):
+        q.qdd_set_sap_variant(P.g, variant)
+        psi, rho = q.qdd_sap_apply(P.g, eta, 4, 8, "f32", nrhs=2, want_rho=True)
+        out[variant] = (psi, rho)
+        assert rel(psi[1], psi_o) <= 2e-5
+    q.qdd_set_sap_variant(P.g, 0)
+    assert rel(out[2][0], out[1][0]) <= 1e-5
+    assert rel(out[2][1], out[1][1]) <= 1e-4
+
+
 def test_sap_nmr_zero_and_multi_rhs(q, ctx, ora):
     P = problem(q, ctx, ora, (8, 8, 8, 8), (4, 4, 4, 4))
     etas = inputs.gaussian_source(P.L, 3003, nrhs=2)
