@@ -525,7 +525,7 @@ __global__ void __launch_bounds__(256) k_sap(const SapArgs<R, SL, SC, SS, SP> a)
 // ---------------------------------------------------------------------------
 // Two threads per site pair.
 //
-// Thread h of a pair (h = lane & 1) takes the hops in directions 2h and 2h+1
+// Thread h of a pair (lanes l and l + 16 of a warp) takes the hops in directions 2h and 2h+1
 // (x, y for h = 0; z, t for h = 1) for both signs, then the pair exchanges
 // partial sums with one shuffle so that thread h holds chirality h (spins
 // 2h, 2h+1), applies clover block h and keeps that half of the MR state.
@@ -616,8 +616,8 @@ struct PairHop {
                 // h = 1 keeps lower (identity order), sends upper
                 cpx<R> send = h ? acc_u[k][c] : acc_l[1 - k][c];
                 cpx<R> keep = h ? acc_l[k][c] : acc_u[k][c];
-                R rre = __shfl_xor_sync(mask, send.re, 1);
-                R rim = __shfl_xor_sync(mask, send.im, 1);
+                R rre = __shfl_xor_sync(mask, send.re, 16);
+                R rim = __shfl_xor_sync(mask, send.im, 16);
                 out[k * 3 + c] = mk<R>(keep.re + rre, keep.im + rim);
             }
     }
@@ -646,7 +646,7 @@ __device__ __forceinline__ void store_half(const Field<S> &f, int64_t rb, int64_
         R m = 0;
 #pragma unroll
         for (int k = 0; k < 6; k++) m = fmax(m, fmax(fabs(x[k].re), fabs(x[k].im)));
-        m = fmax(m, __shfl_xor_sync(mask, m, 1));
+        m = fmax(m, __shfl_xor_sync(mask, m, 16));
         float sc = (float)m;
         if (h == 0) f.scale[sb + (int64_t)d * Vd + s] = sc;
         R inv = m > 0 ? (R)1 / (R)sc : (R)0;
@@ -783,8 +783,11 @@ __global__ void __launch_bounds__(512, 1) k_sap_pair(const SapArgs<R, SL, SC, SS
     extern __shared__ __align__(128) unsigned char smem[];
     const Geom &g = a.g;
     const int Vd = g.Vd, Vh = g.Vh;
+    // lanes l and l+16 of a warp form a pair: each half-warp reads one plane for
+    // 16 consecutive sites, which keeps the 64-bit shared loads free of bank
+    // conflicts (Vd must be a multiple of 32)
     const int t = threadIdx.x;
-    const int i = t >> 1, h = t & 1;
+    const int i = (t >> 5) * 16 + (t & 15), h = (t >> 4) & 1;
     const int d = a.colour * g.Nd2 + blockIdx.x;
     const int se = i, so = Vh + i;
     const R zeta = h ? (R)-1 : (R)1;
@@ -835,7 +838,7 @@ __global__ void __launch_bounds__(512, 1) k_sap_pair(const SapArgs<R, SL, SC, SS
     const int nthreads = Vd;
     const int nwarps = (nthreads + 31) / 32;
     const bool full_warps = (nthreads % 32) == 0;
-    const unsigned mask = nthreads >= 32 ? 0xffffffffu : ((1u << nthreads) - 1u);
+    const unsigned mask = 0xffffffffu;
     const int nphase = a.gather_only ? 0 : 3 + 2 * a.nmr;
 
     for (int rr = 0; rr < a.nrhs; rr++) {
@@ -1052,13 +1055,13 @@ static qdd_status dispatch_staging_v(Gauge *g, const SapArgs<R, SL, SC, SS, SP> 
 }
 
 // Kernel variant: one thread per even/odd site pair, or two (FP32 arithmetic
-// only).  The gauge field's sap_variant selects (0 = automatic: two threads
-// per pair whenever the arithmetic is FP32).
+// and domains of a multiple of 32 sites).  The gauge field's sap_variant
+// selects (0 = automatic: two threads per pair whenever it applies).
 template <typename R, typename SL, typename SC, typename SS, typename SP>
 static qdd_status dispatch_staging(Gauge *g, const SapArgs<R, SL, SC, SS, SP> &a, cudaStream_t s)
 {
     if constexpr (std::is_same<R, float>::value) {
-        if (g->sap_variant != 1) return dispatch_staging_v<R, SL, SC, SS, SP, true>(g, a, s);
+        if (g->sap_variant != 1 && g->hg.Vd % 32 == 0) return dispatch_staging_v<R, SL, SC, SS, SP, true>(g, a, s);
     }
     return dispatch_staging_v<R, SL, SC, SS, SP, false>(g, a, s);
 }
