@@ -68,6 +68,10 @@ def parse():
                     help="workload configuration (2 = the default benchmark line)")
     ap.add_argument("--serve", action="store_true", help="run the serving mix instead of single solves")
     ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--op-bench", action="store_true", help="time only the full-lattice operator")
+    ap.add_argument("--op-lattice", default="32,32,32,64")
+    ap.add_argument("--op-precs", default="f32,f16,df64,f64")
+    ap.add_argument("--op-iters", type=int, default=20)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["qdd", "reference"], default="qdd")
@@ -432,6 +436,50 @@ def run_qdd(args):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------ operator only
+
+def run_op_bench(args):
+    """Full-lattice Wilson-clover operator throughput (1848 flop/site) on a
+    lattice larger than L2, per storage precision, event-timed per launch."""
+    import torch
+
+    from paper_1502_04025_gb300 import build, inputs
+
+    build.build()
+    from paper_1502_04025_gb300 import qdd
+
+    pk, pk_kind = peaks()
+    L = tuple(int(v) for v in args.op_lattice.split(","))
+    ctx = qdd.qdd_create(0, 0)
+    U = inputs.gauge_field(L, DSL["eps"], DSL["gauge_seed"])
+    g = qdd.qdd_create_gauge_field(ctx, L, DSL["dom"], U)
+    del U
+    qdd.qdd_set_clover(g, DSL["csw"], DSL["kappa"])
+    xs = torch.from_numpy(inputs.gaussian_source(L, DSL["source_seed"])).cuda()
+    ys = torch.empty_like(xs)
+    Vl = int(np.prod(L))
+    out = {"metric": "Wilson-clover Dslash throughput", "unit": "GFLOP/s", "lattice": list(L),
+           "domain": list(DSL["dom"]), "flop_per_site": 1848, "peak_hbm_gbs": pk["hbm_gbs"],
+           "peak_kind": "of measured" if pk_kind == "measured" else "of fallback"}
+    bps_of = {"f32": 768, "f16": 392, "bf16": 392, "df64": 1536, "f64": 1536}
+    for prec in args.op_precs.split(","):
+        for _ in range(3):
+            qdd.qdd_apply_D(g, xs, prec, out=ys)
+        qdd.qdd_set_profiling(ctx, qdd.QDD_PROF_DSLASH)
+        qdd.qdd_get_kernel_times(ctx, reset=True)
+        for _ in range(args.op_iters):
+            qdd.qdd_apply_D(g, xs, prec, out=ys)
+        kd = qdd.qdd_get_kernel_times(ctx, reset=True)
+        qdd.qdd_set_profiling(ctx, 0)
+        ms = kd["dslash"][0] / kd["dslash"][1]
+        bps = bps_of[prec]
+        out[prec] = {"ms": ms, "gflops": 1848 * Vl / (ms * 1e-3) / 1e9, "gbs": bps * Vl / (ms * 1e-3) / 1e9,
+                     "frac_hbm": bps * Vl / (ms * 1e-3) / 1e9 / pk["hbm_gbs"], "bytes_per_site": bps}
+    print(json.dumps(out), flush=True)
+    qdd.qdd_destroy_gauge(g)
+    qdd.qdd_destroy(ctx)
+
+
 # ---------------------------------------------------------------- serving
 
 SERVE_LATTICES = [((8, 8, 8, 8), (4, 4, 4, 4)), ((16, 16, 16, 32), (8, 4, 4, 4)),
@@ -525,6 +573,8 @@ def main():
         run_reference(args)
     elif args.serve:
         run_serve(args)
+    elif args.op_bench:
+        run_op_bench(args)
     else:
         run_qdd(args)
 

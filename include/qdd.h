@@ -85,6 +85,13 @@ typedef struct {
     int nrhs;             /* right-hand sides solved together (1..12) */
     int reorth;           /* Gram-Schmidt: 0 classical, 1 classical with
                              selective re-orthogonalisation, 2 twice always */
+    double relax_eta;     /* relaxed Arnoldi operator (inexact Krylov): when
+                             > 0, a step whose residual estimate est satisfies
+                             relax_eta * est <= 0.1 * tol applies w = D z_j in
+                             FP32 (relax_eta = the FP32 operator's relative
+                             error, e.g. 1e-6); 0 = off.  Needs an FP32
+                             preconditioner output.  Convergence is still
+                             decided on the FP64 true residual. */
 } qdd_solve_params;
 
 typedef struct {
@@ -169,8 +176,9 @@ qdd_status qdd_set_clover(qdd_gauge *g, double c_sw, double kappa);
 qdd_status qdd_get_clover(qdd_gauge *g, int which, double *out);
 
 /* Schwarz kernel variant of this gauge field (a tuning choice; results agree
- * to rounding): 0 automatic, 1 one thread per even/odd site pair, 2 two
- * threads per pair (FP32-arithmetic precisions only; FP64 always uses 1). */
+ * to rounding): 0 automatic (= 1), 1 one thread per even/odd site pair, 2 two
+ * threads per pair (FP32-arithmetic precisions and domains of a multiple of
+ * 32 sites; otherwise 1 is used). */
 qdd_status qdd_set_sap_variant(qdd_gauge *g, int variant);
 
 /* ------------------------------------------------------------- operators */
@@ -199,7 +207,8 @@ qdd_status qdd_sap_apply(qdd_gauge *g, const double *eta, double *psi, double *r
 /* ----------------------------------------------------------------- solver */
 
 /* Default parameters: tol 1e-10, m 16, 50 restarts, nmr 4, ncy 4, F32 SAP,
- * F64 Arnoldi operator, SAP on, 1 rhs, selective re-orthogonalisation. */
+ * F64 Arnoldi operator, SAP on, 1 rhs, selective re-orthogonalisation,
+ * no relaxation. */
 void qdd_default_params(qdd_solve_params *p);
 
 /*

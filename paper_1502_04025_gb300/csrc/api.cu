@@ -542,6 +542,7 @@ void qdd_default_params(qdd_solve_params *p)
     p->use_sap = 1;
     p->nrhs = 1;
     p->reorth = 1;
+    p->relax_eta = 0.0;
 }
 
 qdd_status qdd_solve(qdd_gauge *g, const double *b, double *x, int on_device, const qdd_solve_params *p,

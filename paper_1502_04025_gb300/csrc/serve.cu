@@ -39,7 +39,7 @@ static bool same_params(const qdd_solve_params &a, const qdd_solve_params &b)
 {
     return a.tol == b.tol && a.restart_m == b.restart_m && a.max_restarts == b.max_restarts && a.nmr == b.nmr &&
            a.ncy == b.ncy && a.sap_prec == b.sap_prec && a.arnoldi_prec == b.arnoldi_prec &&
-           a.use_sap == b.use_sap && a.reorth == b.reorth;
+           a.use_sap == b.use_sap && a.reorth == b.reorth && a.relax_eta == b.relax_eta;
 }
 
 static void worker_main(Ctx *ctx)

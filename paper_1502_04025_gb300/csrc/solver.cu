@@ -129,14 +129,19 @@ qdd_status solve_impl(Gauge *g, Workspace *wsp, const double *b_in, double *x_ou
     }
     const qdd_prec sp = p->sap_prec;
     const qdd_prec zp = sp == QDD_PREC_F64 ? QDD_PREC_F64 : QDD_PREC_F32;
-    if (p->arnoldi_prec == QDD_PREC_F32 && zp != QDD_PREC_F32) {
+    if ((p->arnoldi_prec == QDD_PREC_F32 || p->relax_eta > 0) && zp != QDD_PREC_F32) {
         set_error("an FP32 Arnoldi operator needs a single-precision preconditioner output");
+        return QDD_EINVAL;
+    }
+    if (!(p->relax_eta >= 0)) {
+        set_error("relax_eta must be >= 0");
         return QDD_EINVAL;
     }
     Workspace &w = *wsp;
     QDD_TRY(ensure_ws(g, w, m, B, sp, p->use_sap != 0));
     if (p->use_sap) QDD_TRY(ensure_copy(g, sp, s));
     if (p->arnoldi_prec != QDD_PREC_F64) QDD_TRY(ensure_copy(g, p->arnoldi_prec, s));
+    if (p->relax_eta > 0) QDD_TRY(ensure_copy(g, QDD_PREC_F32, s));
     const int64_t n = (int64_t)g->hg.V * 12;
     const int64_t ldV = n * B;  // stride between basis vectors of one rhs
     double2 *V = w.V.as<double2>();
@@ -230,8 +235,17 @@ qdd_status solve_impl(Gauge *g, Workspace *wsp, const double *b_in, double *x_ou
             } else {
                 QDD_TRY(launch_spinor_convert(g, vj, nullptr, QDD_PREC_F64, zj, nullptr, zp, B, s));
             }
-            // w = D z_j
-            if (p->arnoldi_prec == QDD_PREC_F64 || p->arnoldi_prec == QDD_PREC_DF64)
+            // w = D z_j; relaxed to FP32 once the residual is small enough
+            // that the operator's error no longer limits the attainable
+            // accuracy (inexact Krylov: error allowed ~ tol / residual)
+            double est_now = 0;
+            for (int r = 0; r < B; r++)
+                if (open[r]) est_now = std::max(est_now, j == 0 ? rel[r] : est[r]);
+            const bool relaxed = p->relax_eta > 0 && p->relax_eta * est_now <= 0.1 * p->tol;
+            if (relaxed)
+                QDD_TRY(launch_dslash(g, QDD_PREC_F32, QDD_PREC_F32, zj, nullptr, QDD_PREC_F32, wv, nullptr,
+                                      QDD_PREC_F64, nullptr, B, s));
+            else if (p->arnoldi_prec == QDD_PREC_F64 || p->arnoldi_prec == QDD_PREC_DF64)
                 QDD_TRY(launch_dslash(g, p->arnoldi_prec, p->arnoldi_prec, zj, nullptr, zp, wv, nullptr,
                                       QDD_PREC_F64, nullptr, B, s));
             else

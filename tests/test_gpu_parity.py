@@ -199,6 +199,19 @@ def test_solve_df64_arnoldi_same_iterations(q, ctx, ora):
     assert rel(x2, x1) <= 1e-9
 
 
+def test_solve_relaxed_arnoldi(q, ctx, ora):
+    """Relaxed (inexact-Krylov) Arnoldi operator: FP32 once the residual is
+    small; still reaches the FP64 true residual with at most one more step."""
+    P = problem(q, ctx, ora, (16, 8, 8, 8), (8, 4, 4, 4), kappa=0.125)
+    b = inputs.gaussian_source(P.L, 2013)
+    x1, r1 = q.qdd_solve(P.g, b, tol=1e-10, sap_prec="f32", arnoldi_prec="f64")
+    x2, r2 = q.qdd_solve(P.g, b, tol=1e-10, sap_prec="f32", arnoldi_prec="f64", relax_eta=1e-6)
+    assert r2["converged"] and _true_rel(ora, P, x2, b) <= 1e-10
+    assert r2["iters"] <= r1["iters"] + 1
+    with pytest.raises(q.QddError):
+        q.qdd_solve(P.g, b, tol=1e-10, sap_prec="f64", relax_eta=1e-6)
+
+
 def test_solve_plain_gmres_and_multi_rhs(q, ctx, ora):
     P = problem(q, ctx, ora, (8, 8, 8, 8), (4, 4, 4, 4))
     bs = np.ascontiguousarray(inputs.point_sources(P.L)[:4])
