@@ -35,12 +35,13 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 WL = dict(L=(16, 16, 16, 32), dom=(8, 4, 4, 4), eps=0.5, csw=1.0, kappa=0.125, gauge_seed=1002, source_seed=2002,
-          nmr=4, ncy=4, m=16, tol=1e-10, sap_prec="f32", arnoldi_prec="df64")
+          nmr=4, ncy=4, m=16, tol=1e-10, sap_prec="f32", arnoldi_prec="df64", relax_eta=1e-6, reorth=0)
 # full-lattice operator throughput: a lattice larger than L2 (32^3x64, eps 0.7, c_sw 1.5, kappa 0.1355)
 DSL = dict(L=(32, 32, 32, 64), dom=(4, 4, 4, 4), eps=0.7, csw=1.5, kappa=0.1355, gauge_seed=1003, source_seed=2003)
 METRIC = "SAP-FGMRES time-to-1e-10 residual"
 WORKLOAD_NAME = ("16^3x32 Wilson-clover, c_sw 1.0, kappa 0.125, eps 0.5 links; SAP-FGMRES(16), 8x4x4x4 domains, "
-                 "nmr 4, ncy 4, FP32 preconditioner, FP64 outer (double-float Arnoldi operator), tol 1e-10, "
+                 "nmr 4, ncy 4, FP32 preconditioner, FP64 outer (Gram-Schmidt, least squares, solution, true "
+                 "residual; double-float Arnoldi operator relaxed to FP32 below est 1e-5), tol 1e-10, "
                  "1 Gaussian source")
 SAP_FLOP = {"hop": 1320, "clover": 504, "combine": 24, "mr_blas": 336, "boundary_hop": 168}
 L2_FLUSH_BYTES = 256 << 20
@@ -53,10 +54,12 @@ CONFIGS = {
             name="8^4 plain FP64 SAP-FGMRES(16), 4^4 domains, c_sw 1.0, kappa 0.12, eps 0.5"),
     2: dict(WL, source="gaussian", nrhs=1, name=WORKLOAD_NAME),
     3: dict(L=(32, 32, 32, 64), dom=(4, 4, 4, 4), eps=0.7, csw=1.5, kappa=0.1355, gauge_seed=1003, source_seed=2003,
-            nmr=4, ncy=4, m=16, tol=1e-10, sap_prec="f16", arnoldi_prec="df64", source="point12", nrhs=12,
+            nmr=4, ncy=4, m=16, tol=1e-10, sap_prec="f16", arnoldi_prec="df64", relax_eta=1e-6, reorth=0,
+            source="point12", nrhs=12,
             name="32^3x64, eps 0.7, c_sw 1.5, kappa 0.1355, FP16-stored SAP, FP64 outer, 12 point sources batched"),
     4: dict(L=(48, 48, 48, 96), dom=(4, 4, 4, 4), eps=0.7, csw=1.5, kappa=0.1355, gauge_seed=1004, source_seed=2004,
-            nmr=4, ncy=4, m=16, tol=1e-10, sap_prec="bf16", arnoldi_prec="df64", source="z2", nrhs=1,
+            nmr=4, ncy=4, m=16, tol=1e-10, sap_prec="bf16", arnoldi_prec="df64", relax_eta=1e-6, reorth=0,
+            source="z2", nrhs=1,
             name="48^3x96, eps 0.7, c_sw 1.5, kappa 0.1355, BF16-stored SAP, FP64 FGMRES(16), Z2 source"),
 }
 
@@ -276,7 +279,7 @@ def run_qdd(args):
     qdd.qdd_set_clover(g, W["csw"], W["kappa"])
     params = qdd.qdd_default_params(tol=W["tol"], restart_m=W["m"], nmr=W["nmr"], ncy=W["ncy"],
                                     sap_prec=W["sap_prec"], arnoldi_prec=W["arnoldi_prec"], max_restarts=200,
-                                    nrhs=nrhs)
+                                    nrhs=nrhs, relax_eta=W.get("relax_eta", 0.0), reorth=W.get("reorth", 1))
     bd = torch.from_numpy(b).cuda()
     xd = torch.empty_like(bd)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -421,6 +424,7 @@ def run_qdd(args):
                            "domain": list(W["dom"]), "kappa": W["kappa"], "c_sw": W["csw"], "eps": W["eps"],
                            "nmr": W["nmr"], "ncy": W["ncy"], "restart_m": W["m"], "tol": W["tol"], "nrhs": nrhs,
                            "sap_prec": W["sap_prec"], "arnoldi_prec": W["arnoldi_prec"],
+                           "relax_eta": W.get("relax_eta", 0.0), "reorth": W.get("reorth", 1),
                            "l2": "256 MB buffer written before every step; Krylov working set larger than L2",
                            "parallelism": f"{world} replica(s)"},
                 "iters": last["iters"], "restarts": last["restarts"], "true_rel_res": last["true_rel_res"],
@@ -517,7 +521,8 @@ def run_serve(args):
         ki = int(rng.integers(0, len(SERVE_KAPPAS)))
         nrhs = int(rng.integers(1, 13))
         reqs.append((li, ki, nrhs))
-    params = {r: qdd.qdd_default_params(tol=1e-10, sap_prec="f32", arnoldi_prec="df64", nrhs=r, max_restarts=200)
+    params = {r: qdd.qdd_default_params(tol=1e-10, sap_prec="f32", arnoldi_prec="df64", nrhs=r, max_restarts=200,
+                                        relax_eta=1e-6, reorth=0)
               for r in range(1, 13)}
     srcs = {}
     for li, (L, dom) in enumerate(SERVE_LATTICES):

@@ -277,6 +277,34 @@ double qdd_domain_working_set(const int dom[4], int link_bytes, int n_full, int 
  */
 qdd_status qdd_layout(const int L[4], const int dom[4], int *site_of, uint16_t *nbl, int *nbd);
 
+/* ------------------------------------------------------------------ tuning */
+
+typedef struct {
+    int dom[4];        /* fastest domain shape */
+    int sap_variant;   /* its Schwarz kernel variant (qdd_set_sap_variant) */
+    int nmr;           /* its MR step count */
+    int iters;         /* Arnoldi steps it needed */
+    int n_tried;       /* candidates timed */
+    double ms;         /* its time-to-solution (CUDA events) */
+    double wave_load;  /* x/ceil(x), x = domains per colour / SMs (Sec. 3.5) */
+} qdd_tune_result;
+
+/*
+ * Autotuner (the paper picks the domain size by cache capacity, Sec. 3.3, and
+ * the MR step count by time-to-solution, Sec. 3.7): for every domain shape in
+ * dom_candidates (n_dom x 4 ints), both Schwarz kernel variants where they
+ * apply, and every MR step count in nmr_candidates (or p->nmr if n_nmr = 0),
+ * build the gauge field, run the caller's solve (b: host layout, host or
+ * device) once untimed and once timed, and return the fastest converged
+ * setting.  log (may be NULL) receives a JSON array with every candidate's
+ * time, iteration count and wave load.  Shapes the geometry rules reject are
+ * logged and skipped.  Returns QDD_ENOCONV if no candidate converged.
+ */
+qdd_status qdd_autotune(qdd_ctx *ctx, const int L[4], const double *links, int links_on_device, double c_sw,
+                        double kappa, const double *b, int b_on_device, const qdd_solve_params *p,
+                        const int *dom_candidates, int n_dom, const int *nmr_candidates, int n_nmr,
+                        qdd_tune_result *out, char *log, size_t log_len);
+
 /* ---------------------------------------------------------------- serving */
 
 /*

@@ -310,6 +310,9 @@ qdd_status qdd_create_gauge_field(qdd_ctx *ctx, const int L[4], const int dom[4]
     QDD_TRY(g->d_nbl.alloc(ctx, hg.nbl.size() * sizeof(uint16_t)));
     QDD_TRY(g->d_nbd.alloc(ctx, hg.nbd.size() * sizeof(int)));
     QDD_TRY(g->d_site_of.alloc(ctx, hg.site_of.size() * sizeof(int)));
+    QDD_TRY(g->d_block_slot.alloc(ctx, hg.block_slot.size() * sizeof(int)));
+    QDD_CUDA(cudaMemcpy(g->d_block_slot.p, hg.block_slot.data(), hg.block_slot.size() * sizeof(int),
+                        cudaMemcpyHostToDevice));
     QDD_CUDA(cudaMemcpy(g->d_nbl.p, hg.nbl.data(), hg.nbl.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
     QDD_CUDA(cudaMemcpy(g->d_nbd.p, hg.nbd.data(), hg.nbd.size() * sizeof(int), cudaMemcpyHostToDevice));
     QDD_CUDA(cudaMemcpy(g->d_site_of.p, hg.site_of.data(), hg.site_of.size() * sizeof(int),
@@ -330,6 +333,7 @@ qdd_status qdd_create_gauge_field(qdd_ctx *ctx, const int L[4], const int dom[4]
         if ((1 << k) == hg.Vd) G.vd_shift = k;
     G.nbl = g->d_nbl.as<uint16_t>();
     G.nbd = g->d_nbd.as<int>();
+    G.block_slot = g->d_block_slot.as<int>();
 
     const size_t lbytes = (size_t)hg.V * 36 * sizeof(double2);
     QDD_TRY(g->links64.alloc(ctx, lbytes));

@@ -162,7 +162,25 @@ struct Geom {
     int vd_shift;          // log2(Vd) when Vd is a power of two, else -1
     const uint16_t *nbl;   // [Vd][8]: neighbour site slot (wrapped into the domain), bit 15 = leaves the domain
     const int *nbd;        // [Nd][8]: neighbour domain slot
+    const int *block_slot; // [Nd]: slot of the domain with lexicographic block index b
 };
+
+// Site of thread index gi when the lattice is walked domain by domain in
+// lexicographic block order (neighbouring domains close together in time, so
+// their data is still in L2 when it is read as a neighbour); the storage
+// order of the slots is colour-major.
+__device__ __forceinline__ void lex_site(const Geom &g, int gi, int &d, int &s)
+{
+    int b;
+    if (g.vd_shift >= 0) {
+        b = gi >> g.vd_shift;
+        s = gi & (g.Vd - 1);
+    } else {
+        b = gi / g.Vd;
+        s = gi - b * g.Vd;
+    }
+    d = __ldg(g.block_slot + b);
+}
 
 constexpr uint16_t kCross = 0x8000;
 constexpr uint16_t kSlotMask = 0x7fff;

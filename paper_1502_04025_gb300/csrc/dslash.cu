@@ -5,7 +5,9 @@
 //
 // One thread per site over the domain-blocked, plane-major layout: a warp
 // reads 32 consecutive sites of one plane (256 or 512 contiguous bytes) for
-// every link, clover and spinor component.  Neighbour sites come from a
+// every link, clover and spinor component.  Domains are visited in
+// lexicographic block order, so a domain's neighbours are processed close in
+// time and their spinors are read from L2 rather than again from HBM.  Neighbour sites come from a
 // per-domain-shape table (the neighbour's slot inside its domain and whether
 // the hop leaves the domain) and a per-domain table of neighbouring domains.
 // The roofline of this kernel is HBM bandwidth: each link, clover entry and
@@ -60,7 +62,7 @@ __device__ __forceinline__ void dslash_dir(const Geom &g, const Field<SL> &U, co
 }
 
 template <typename R, typename SL, typename SC, typename SI, typename SO, bool RESID>
-__global__ void __launch_bounds__(128) k_dslash(Geom g, Field<SL> U, Field<SC> A, Field<SI> in, Field<SO> out,
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 1) k_dslash(Geom g, Field<SL> U, Field<SC> A, Field<SI> in, Field<SO> out,
                                                 const double2 *b, R kappa)
 {
     int gi = blockIdx.x * blockDim.x + threadIdx.x;
@@ -68,7 +70,8 @@ __global__ void __launch_bounds__(128) k_dslash(Geom g, Field<SL> U, Field<SC> A
     const int64_t r = blockIdx.y;
     const int64_t rbase = r * (int64_t)g.V * 12, sbase = r * (int64_t)g.V;
     int d, s;
-    split_index(g, gi, d, s);
+    lex_site(g, gi, d, s);
+    gi = d * g.Vd + s;
     cpx<R> acc[12];
 #pragma unroll
     for (int k = 0; k < 12; k++) acc[k] = mk<R>(0, 0);
@@ -222,7 +225,7 @@ __global__ void __launch_bounds__(128) k_dslash_df(Geom g, const float4 *U, cons
     if (gi >= g.V) return;
     const int64_t rbase = (int64_t)blockIdx.y * g.V * 12;
     int d, s;
-    split_index(g, gi, d, s);
+    lex_site(g, gi, d, s);
     cdfacc acc[12];
 #pragma unroll
     for (int k = 0; k < 12; k++) cdfacc_zero(acc[k]);

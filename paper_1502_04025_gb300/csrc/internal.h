@@ -126,6 +126,7 @@ struct HostGeom {
     int L[4], dom[4], nb[4];
     int V, Vd, Vh, Nd, Nd2;
     std::vector<int> slot_block;   // slot -> block index
+    std::vector<int> block_slot;   // lexicographic block index -> slot
     std::vector<int> site_of;      // internal index -> host site index
     std::vector<uint16_t> nbl;     // [Vd][8]
     std::vector<int> nbd;          // [Nd][8]
@@ -158,7 +159,7 @@ struct Gauge {
     Ctx *ctx = nullptr;
     HostGeom hg;
     Geom geom{};
-    DevMem d_nbl, d_nbd, d_site_of;
+    DevMem d_nbl, d_nbd, d_site_of, d_block_slot;
     DevMem links64;           // FP64 links, internal layout
     bool have_clover = false;
     double csw = 0, kappa = 0;

@@ -75,7 +75,8 @@ qdd_status make_geometry(const int L[4], const int dom[4], HostGeom &hg)
 
     // slot <-> block: slot = colour*Nd/2 + (block >> 1)
     hg.slot_block.assign(hg.Nd, -1);
-    std::vector<int> block_slot(hg.Nd);
+    hg.block_slot.assign(hg.Nd, -1);
+    std::vector<int> &block_slot = hg.block_slot;
     for (int b = 0; b < hg.Nd; b++) {
         int bc[4], t = b;
         for (int mu = 0; mu < 4; mu++) {

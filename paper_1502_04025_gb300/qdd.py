@@ -49,6 +49,12 @@ class qdd_report(ctypes.Structure):
         return d
 
 
+class qdd_tune_result(ctypes.Structure):
+    _fields_ = [("dom", ctypes.c_int * 4), ("sap_variant", ctypes.c_int), ("nmr", ctypes.c_int),
+                ("iters", ctypes.c_int), ("n_tried", ctypes.c_int), ("ms", ctypes.c_double),
+                ("wave_load", ctypes.c_double)]
+
+
 _vp = ctypes.c_void_p
 _ip = ctypes.POINTER(ctypes.c_int)
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -77,6 +83,9 @@ _SIGS = {
     "qdd_load_model": (ctypes.c_double, [ctypes.c_double, ctypes.c_double]),
     "qdd_domain_working_set": (ctypes.c_double, [_ip, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "qdd_layout": (ctypes.c_int, [_ip, _ip, _vp, _vp, _vp]),
+    "qdd_autotune": (ctypes.c_int, [_vp, _ip, _vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, _vp, ctypes.c_int,
+                                    ctypes.POINTER(qdd_solve_params), _ip, ctypes.c_int, _ip, ctypes.c_int,
+                                    ctypes.POINTER(qdd_tune_result), ctypes.c_char_p, ctypes.c_size_t]),
     "qdd_submit": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.POINTER(qdd_solve_params),
                                   ctypes.POINTER(ctypes.c_uint64)]),
     "qdd_poll": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.POINTER(qdd_report), ctypes.c_double]),
@@ -299,6 +308,25 @@ def qdd_layout(L, dom):
     _check(_lib.qdd_layout(_ivec(L), _ivec(dom), site_of.ctypes.data, nbl.ctypes.data, nbd.ctypes.data),
            "qdd_layout")
     return site_of, nbl.reshape(Vd, 8), nbd.reshape(Nd, 8)
+
+
+def qdd_autotune(ctx, L, links, c_sw: float, kappa: float, b, params: qdd_solve_params, dom_candidates,
+                 nmr_candidates=()):
+    """Fastest (dom, kernel variant, nmr) for this problem; returns (result dict, per-candidate log)."""
+    import json
+
+    pl, ldev = _ptr(links)
+    pb, bdev = _ptr(b)
+    doms = (ctypes.c_int * (4 * len(dom_candidates)))(*[int(v) for d in dom_candidates for v in d])
+    nmrs = (ctypes.c_int * max(1, len(nmr_candidates)))(*[int(v) for v in nmr_candidates])
+    res = qdd_tune_result()
+    buf = ctypes.create_string_buffer(1 << 16)
+    _check(_lib.qdd_autotune(ctx, _ivec(L), pl, ldev, float(c_sw), float(kappa), pb, bdev, ctypes.byref(params),
+                             doms, len(dom_candidates), nmrs, len(nmr_candidates), ctypes.byref(res), buf,
+                             len(buf)), "qdd_autotune")
+    out = {"dom": tuple(res.dom), "sap_variant": res.sap_variant, "nmr": res.nmr, "iters": res.iters,
+           "n_tried": res.n_tried, "ms": res.ms, "wave_load": res.wave_load}
+    return out, json.loads(buf.value.decode())
 
 
 # ---------------------------------------------------------------- serving

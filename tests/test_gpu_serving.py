@@ -104,6 +104,35 @@ def test_admission_rejects_what_cannot_fit(q):
     q.qdd_destroy(ctx)
 
 
+def test_autotune_picks_a_converged_shape(q, ora):
+    """The autotuner times every candidate and returns the fastest converged
+    one; shapes the geometry rules reject are logged and skipped."""
+    ctx = q.qdd_create(0, 0)
+    L = (16, 8, 8, 8)
+    U = inputs.gauge_field(L, 0.5, 1001)
+    b = inputs.gaussian_source(L, 2001)
+    p = q.qdd_default_params(tol=1e-10, sap_prec="f32")
+    cands = [(4, 4, 4, 4), (8, 4, 4, 4), (4, 2, 2, 2), (16, 4, 4, 4)]  # the last leaves one block in x
+    res, log = q.qdd_autotune(ctx, L, U, 1.0, 0.125, b, p, cands, nmr_candidates=(2, 4))
+    timed = [c for c in log if "ms" in c]
+    assert res["n_tried"] == len(timed) and len(timed) >= 6
+    assert any("error" in c for c in log)
+    best = min((c for c in timed if c["converged"]), key=lambda c: c["ms"])
+    assert tuple(best["dom"]) == res["dom"] and best["nmr"] == res["nmr"]
+    for c in timed:
+        assert 0 < c["wave_load"] <= 1
+    # the chosen setting solves the problem
+    g = q.qdd_create_gauge_field(ctx, L, res["dom"], U)
+    q.qdd_set_clover(g, 1.0, 0.125)
+    q.qdd_set_sap_variant(g, res["sap_variant"])
+    x, rep = q.qdd_solve(g, b, q.qdd_default_params(tol=1e-10, sap_prec="f32", nmr=res["nmr"]))
+    A = ora.clover(L, U, 1.0, 0.125)
+    r = b - ora.apply_D(L, U, A, 0.125, x)
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1e-10
+    q.qdd_destroy_gauge(g)
+    q.qdd_destroy(ctx)
+
+
 def test_poll_unknown_ticket_and_timeout(q):
     ctx = q.qdd_create(0, 0)
     st, _ = q.qdd_poll(ctx, 12345, 0.0)
