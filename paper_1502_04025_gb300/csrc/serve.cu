@@ -100,17 +100,20 @@ static void worker_main(Ctx *ctx)
             }
             ctx->running++;
         }
-        // ---- run the batch
+        // ---- run the batch (a single request solves straight from/to its own buffers)
         const Gauge *g = batch[0]->g;
         const size_t per = (size_t)g->hg.V * 24;
         int total = 0;
         for (auto &r : batch) total += r->p.nrhs;
-        bm.resize(per * total);
-        xm.resize(per * total);
+        const bool single = batch.size() == 1;
         size_t off = 0;
-        for (auto &r : batch) {
-            std::memcpy(bm.data() + off, r->b.data(), r->b.size() * sizeof(double));
-            off += r->b.size();
+        if (!single) {
+            bm.resize(per * total);
+            xm.resize(per * total);
+            for (auto &r : batch) {
+                std::memcpy(bm.data() + off, r->b.data(), r->b.size() * sizeof(double));
+                off += r->b.size();
+            }
         }
         qdd_solve_params pm = batch[0]->p;
         pm.nrhs = total;
@@ -119,7 +122,9 @@ static void worker_main(Ctx *ctx)
         size_t need = workspace_bytes(batch[0]->g, pm.restart_m, total, pm.sap_prec, pm.use_sap != 0);
         if (workspace_held(ws.get()) > 2 * need) workspace_release(ws.get());
         clear_error();
-        qdd_status s = solve_impl(batch[0]->g, ws.get(), bm.data(), xm.data(), 0, &pm, &rep, st, &rel);
+        qdd_status s = single ? solve_impl(batch[0]->g, ws.get(), batch[0]->b.data(), batch[0]->x, 0, &pm, &rep, st,
+                                           &rel)
+                              : solve_impl(batch[0]->g, ws.get(), bm.data(), xm.data(), 0, &pm, &rep, st, &rel);
         std::string msg = s == QDD_OK ? std::string() : std::string(qdd_last_error());
         auto t_done = std::chrono::steady_clock::now();
         {
@@ -127,7 +132,7 @@ static void worker_main(Ctx *ctx)
             off = 0;
             int r0 = 0;
             for (auto &r : batch) {
-                std::memcpy(r->x, xm.data() + off, r->b.size() * sizeof(double));
+                if (!single) std::memcpy(r->x, xm.data() + off, r->b.size() * sizeof(double));
                 off += r->b.size();
                 r->rep = rep;
                 double tr = 0;
@@ -141,10 +146,17 @@ static void worker_main(Ctx *ctx)
                 r->status = (s == QDD_ENOCONV && r->rep.converged) ? QDD_OK : s;
                 r->err = msg;
                 r->done = true;
+                std::vector<double>().swap(r->b);  // the source copy is no longer needed
                 r0 += r->p.nrhs;
             }
             ctx->running--;
         }
+        // a large idle workspace would block the admission of other requests:
+        // give it back (small ones are kept for reuse)
+        if (workspace_held(ws.get()) > ((size_t)4 << 30)) workspace_release(ws.get());
+        // keep the merge buffers only while they are small
+        if (bm.size() > ((size_t)1 << 27)) std::vector<double>().swap(bm);
+        if (xm.size() > ((size_t)1 << 27)) std::vector<double>().swap(xm);
         ctx->done_cv.notify_all();
         ctx->q_cv.notify_all();
     }
