@@ -219,6 +219,17 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ GPU leg
 
+def max_over_ranks(value: float, dist=None, device: str = "cpu") -> float:
+    """The slowest rank's time (all ranks receive it); value itself with one rank."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    import torch
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def make_sources(W):
     from paper_1502_04025_gb300 import inputs
 
@@ -312,11 +323,7 @@ def run_qdd(args):
     ms_total = e0.elapsed_time(e1)
     kt = qdd.qdd_get_kernel_times(ctx, reset=True)
     qdd.qdd_set_profiling(ctx, 0)
-    ms_step = ms_total / args.steps
-    if dist is not None:
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = max_over_ranks(ms_total / args.steps, dist, "cuda")
     launches = int(sum(r["kernel_launches"] for r in reps))
 
     # ---- kernel-class shares from one extra solve with every class event-timed

@@ -48,6 +48,21 @@ void Timer::begin(int cls, cudaStream_t s, cudaEvent_t *a)
     }
 }
 
+void Timer::begin_seq(int cls, cudaStream_t s, cudaEvent_t *a)
+{
+    std::lock_guard<std::mutex> lk(mu);
+    if (mask & (1 << cls)) {
+        *a = get_event();
+        cudaEventRecord(*a, s);
+    }
+}
+
+void Timer::count(int cls)
+{
+    std::lock_guard<std::mutex> lk(mu);
+    launches[cls]++;
+}
+
 void Timer::end(int cls, cudaStream_t s, cudaEvent_t a)
 {
     if (!a) return;
@@ -511,8 +526,12 @@ qdd_status qdd_sap_apply(qdd_gauge *g, const double *eta, double *psi, double *r
     QDD_TRY(launch_spinor_in(g, din, st->a.p, st->a_s.as<float>(), prec, nrhs, s));
     if (n_half < 2) QDD_CUDA(cudaMemsetAsync(st->c.p, 0, V * 12 * elem_bytes(pp) * nrhs, s));
     SapBuffers b{st->a.p, st->b.p, st->c.p, st->a_s.as<float>(), st->b_s.as<float>()};
-    for (int hs = 0; hs < n_half; hs++)
-        QDD_TRY(launch_sap_halfsweep(g, prec, b, hs & 1, nmr, nrhs, hs < 2, hs >= 1, 0, st->err.as<int>(), s));
+    {
+        SeqScope seq(g->ctx->timer, K_SAP, s);
+        for (int hs = 0; hs < n_half; hs++)
+            QDD_TRY(launch_sap_halfsweep(g, prec, b, hs & 1, nmr, nrhs, hs < 2, hs >= 1, 0, st->err.as<int>(), s,
+                                         hs >= 1, false));
+    }
     if (rho)  // bring the residual of the next colour up to date
         QDD_TRY(launch_sap_halfsweep(g, prec, b, n_half & 1, nmr, nrhs, 0, 1, 1, st->err.as<int>(), s));
     double *dout = nullptr;

@@ -61,6 +61,8 @@ struct Timer {
 
     cudaEvent_t get_event();
     void begin(int cls, cudaStream_t s, cudaEvent_t *a);
+    void begin_seq(int cls, cudaStream_t s, cudaEvent_t *a);  // events, no launch count
+    void count(int cls);                                      // launch count only
     void end(int cls, cudaStream_t s, cudaEvent_t a);
     void resolve();  // after the stream has been synchronised
     ~Timer();
@@ -71,8 +73,26 @@ struct LaunchScope {
     int cls;
     cudaStream_t s;
     cudaEvent_t a = nullptr;
-    LaunchScope(Timer &t_, int cls_, cudaStream_t s_) : t(t_), cls(cls_), s(s_) { t.begin(cls, s, &a); }
+    // timed = false: count the launch, but leave its timing to an enclosing
+    // scope (a sequence of dependent launches timed as one, see SapScope)
+    LaunchScope(Timer &t_, int cls_, cudaStream_t s_, bool timed = true) : t(t_), cls(cls_), s(s_)
+    {
+        if (timed) t.begin(cls, s, &a);
+        else t.count(cls);
+    }
     ~LaunchScope() { t.end(cls, s, a); }
+};
+
+// Events around a whole preconditioner application (2*ncy half-sweep launches
+// that overlap through programmatic dependent launch); the time lands in the
+// class without adding to its launch count.
+struct SeqScope {
+    Timer &t;
+    int cls;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr;
+    SeqScope(Timer &t_, int cls_, cudaStream_t s_) : t(t_), cls(cls_), s(s_) { t.begin_seq(cls, s, &a); }
+    ~SeqScope() { t.end(cls, s, a); }
 };
 
 // ------------------------------------------------------------------- memory
@@ -215,8 +235,13 @@ struct SapBuffers {
 };
 // gather_only: apply the pending inter-domain update to the residual of the
 // domains of `colour` and store it, without a block solve.
+// pdl: launch as a programmatic dependent of the previous half-sweep (its
+// CTAs may start early and stage read-only data; it must directly follow a
+// half-sweep in the stream).  timed: bracket this launch with profiling
+// events (false when the caller times a whole preconditioner application).
 qdd_status launch_sap_halfsweep(Gauge *g, qdd_prec prec, const SapBuffers &b, int colour, int nmr, int nrhs,
-                                int first_psi, int gather, int gather_only, int *d_err, cudaStream_t s);
+                                int first_psi, int gather, int gather_only, int *d_err, cudaStream_t s,
+                                bool pdl = false, bool timed = true);
 size_t sap_smem_bytes(const HostGeom &hg, qdd_prec prec, bool stage_links, bool stage_clover);
 
 // blas.cu (FP64 complex vectors of n elements, stored as double2; scratch holds

@@ -79,6 +79,12 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return false;
 }
 
+// Programmatic dependent launch: let the next half-sweep's CTAs start (they
+// stage their read-only domain data), and wait for the previous grid's
+// results before reading them.  Both are no-ops without a dependent launch.
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // copy bytes (multiple of 16, both addresses 16-aligned) in chunks
 __device__ __forceinline__ void bulk_g2s_chunked(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
 {
@@ -300,6 +306,7 @@ template <typename R, typename SL, typename SC, typename SS, typename SP, bool S
 __global__ void __launch_bounds__(256) k_sap(const SapArgs<R, SL, SC, SS, SP> a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
+    pdl_launch_dependents();
     const Geom &g = a.g;
     const int Vd = g.Vd, Vh = g.Vh;
     const int i = threadIdx.x;
@@ -354,6 +361,7 @@ __global__ void __launch_bounds__(256) k_sap(const SapArgs<R, SL, SC, SS, SP> a)
     const bool full_warps = (Vh % 32) == 0;
     const int nphase = a.gather_only ? 0 : 3 + 2 * a.nmr;
 
+    pdl_wait();  // the previous half-sweep's rho, delta and psi are visible from here on
     for (int rr = 0; rr < a.nrhs; rr++) {
         const int64_t rb = rr * a.rstride, sb = rr * a.sstride;
 
@@ -781,6 +789,7 @@ template <typename R, typename SL, typename SC, typename SS, typename SP, bool S
 __global__ void __launch_bounds__(512, 1) k_sap_pair(const SapArgs<R, SL, SC, SS, SP> a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
+    pdl_launch_dependents();
     const Geom &g = a.g;
     const int Vd = g.Vd, Vh = g.Vh;
     // lanes l and l+16 of a warp form a pair: each half-warp reads one plane for
@@ -841,6 +850,7 @@ __global__ void __launch_bounds__(512, 1) k_sap_pair(const SapArgs<R, SL, SC, SS
     const unsigned mask = 0xffffffffu;
     const int nphase = a.gather_only ? 0 : 3 + 2 * a.nmr;
 
+    pdl_wait();  // the previous half-sweep's rho, delta and psi are visible from here on
     for (int rr = 0; rr < a.nrhs; rr++) {
         const int64_t rb = rr * a.rstride, sb = rr * a.sstride;
 
@@ -1009,7 +1019,7 @@ __global__ void __launch_bounds__(512, 1) k_sap_pair(const SapArgs<R, SL, SC, SS
 // ---------------------------------------------------------------- launch
 
 template <typename R, typename SL, typename SC, typename SS, typename SP, bool STL, bool STC, bool PAIR>
-static qdd_status run_sap(Gauge *g, const SapArgs<R, SL, SC, SS, SP> &a, cudaStream_t s)
+static qdd_status run_sap(Gauge *g, const SapArgs<R, SL, SC, SS, SP> &a, cudaStream_t s, bool pdl, bool timed)
 {
     const HostGeom &hg = g->hg;
     size_t smem = sap_smem_layout<R, SL, SC>(hg.Vd, STL, STC);
@@ -1022,9 +1032,18 @@ static qdd_status run_sap(Gauge *g, const SapArgs<R, SL, SC, SS, SP> &a, cudaStr
         QDD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         configured = smem;
     }
-    LaunchScope ls(g->ctx->timer, K_SAP, s);
-    kern<<<hg.Nd2, PAIR ? hg.Vd : hg.Vh, smem, s>>>(a);
-    QDD_CUDA(cudaGetLastError());
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(hg.Nd2);
+    cfg.blockDim = dim3(PAIR ? hg.Vd : hg.Vh);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    LaunchScope ls(g->ctx->timer, K_SAP, s, timed);
+    QDD_CUDA(cudaLaunchKernelEx(&cfg, kern, a));
     return QDD_OK;
 }
 
@@ -1041,15 +1060,17 @@ static size_t smem_limit()
 }
 
 template <typename R, typename SL, typename SC, typename SS, typename SP, bool PAIR>
-static qdd_status dispatch_staging_v(Gauge *g, const SapArgs<R, SL, SC, SS, SP> &a, cudaStream_t s)
+static qdd_status dispatch_staging_v(Gauge *g, const SapArgs<R, SL, SC, SS, SP> &a, cudaStream_t s, bool pdl,
+                                     bool timed)
 {
     const int Vd = g->hg.Vd;
     const size_t lim = smem_limit();
-    if (sap_smem_layout<R, SL, SC>(Vd, true, true) <= lim) return run_sap<R, SL, SC, SS, SP, true, true, PAIR>(g, a, s);
+    if (sap_smem_layout<R, SL, SC>(Vd, true, true) <= lim)
+        return run_sap<R, SL, SC, SS, SP, true, true, PAIR>(g, a, s, pdl, timed);
     if (sap_smem_layout<R, SL, SC>(Vd, true, false) <= lim)
-        return run_sap<R, SL, SC, SS, SP, true, false, PAIR>(g, a, s);
+        return run_sap<R, SL, SC, SS, SP, true, false, PAIR>(g, a, s, pdl, timed);
     if (sap_smem_layout<R, SL, SC>(Vd, false, false) <= lim)
-        return run_sap<R, SL, SC, SS, SP, false, false, PAIR>(g, a, s);
+        return run_sap<R, SL, SC, SS, SP, false, false, PAIR>(g, a, s, pdl, timed);
     set_error("domain of %d sites does not fit in shared memory", Vd);
     return QDD_EINVAL;
 }
@@ -1059,12 +1080,14 @@ static qdd_status dispatch_staging_v(Gauge *g, const SapArgs<R, SL, SC, SS, SP> 
 // selects (0 = automatic = one thread per pair, measured faster on GB300:
 // the pair form halves the registers but issues 30% more instructions).
 template <typename R, typename SL, typename SC, typename SS, typename SP>
-static qdd_status dispatch_staging(Gauge *g, const SapArgs<R, SL, SC, SS, SP> &a, cudaStream_t s)
+static qdd_status dispatch_staging(Gauge *g, const SapArgs<R, SL, SC, SS, SP> &a, cudaStream_t s, bool pdl,
+                                   bool timed)
 {
     if constexpr (std::is_same<R, float>::value) {
-        if (g->sap_variant == 2 && g->hg.Vd % 32 == 0) return dispatch_staging_v<R, SL, SC, SS, SP, true>(g, a, s);
+        if (g->sap_variant == 2 && g->hg.Vd % 32 == 0)
+            return dispatch_staging_v<R, SL, SC, SS, SP, true>(g, a, s, pdl, timed);
     }
-    return dispatch_staging_v<R, SL, SC, SS, SP, false>(g, a, s);
+    return dispatch_staging_v<R, SL, SC, SS, SP, false>(g, a, s, pdl, timed);
 }
 
 size_t sap_smem_bytes(const HostGeom &hg, qdd_prec prec, bool stl, bool stc)
@@ -1078,7 +1101,8 @@ size_t sap_smem_bytes(const HostGeom &hg, qdd_prec prec, bool stl, bool stc)
 }
 
 qdd_status launch_sap_halfsweep(Gauge *g, qdd_prec prec, const SapBuffers &b, int colour, int nmr, int nrhs,
-                                int first_psi, int gather, int gather_only, int *d_err, cudaStream_t s)
+                                int first_psi, int gather, int gather_only, int *d_err, cudaStream_t s, bool pdl,
+                                bool timed)
 {
     QDD_TRY(ensure_copy(g, prec, s));
     const int64_t rs = (int64_t)g->hg.V * 12, ss = g->hg.V;
@@ -1089,28 +1113,28 @@ qdd_status launch_sap_halfsweep(Gauge *g, qdd_prec prec, const SapBuffers &b, in
             g->geom, {g->links64.as<double2>(), nullptr}, {g->sclov64.as<double2>(), nullptr},
             {(double2 *)b.rho, nullptr}, {(double2 *)b.delta, nullptr}, {(double2 *)b.psi, nullptr},
             rs, ss, g->kappa, colour, nmr, nrhs, first_psi, gather, gather_only, d_err};
-        return dispatch_staging(g, a, s);
+        return dispatch_staging(g, a, s, pdl, timed);
     }
     case QDD_PREC_F32: {
         SapArgs<float, StF32, StF32, StF32, StF32> a{
             g->geom, {c.links.as<float2>(), nullptr}, {c.sclov.as<float2>(), nullptr},
             {(float2 *)b.rho, nullptr}, {(float2 *)b.delta, nullptr}, {(float2 *)b.psi, nullptr},
             rs, ss, (float)g->kappa, colour, nmr, nrhs, first_psi, gather, gather_only, d_err};
-        return dispatch_staging(g, a, s);
+        return dispatch_staging(g, a, s, pdl, timed);
     }
     case QDD_PREC_F16S: {
         SapArgs<float, StF16, StF16, StF16, StF32> a{
             g->geom, {c.links.as<__half2>(), nullptr}, {c.sclov.as<__half2>(), c.sclov_s.as<float>()},
             {(__half2 *)b.rho, b.rho_s}, {(__half2 *)b.delta, b.delta_s}, {(float2 *)b.psi, nullptr},
             rs, ss, (float)g->kappa, colour, nmr, nrhs, first_psi, gather, gather_only, d_err};
-        return dispatch_staging(g, a, s);
+        return dispatch_staging(g, a, s, pdl, timed);
     }
     case QDD_PREC_BF16S: {
         SapArgs<float, StBF16, StBF16, StBF16, StF32> a{
             g->geom, {c.links.as<__nv_bfloat162>(), nullptr}, {c.sclov.as<__nv_bfloat162>(), c.sclov_s.as<float>()},
             {(__nv_bfloat162 *)b.rho, b.rho_s}, {(__nv_bfloat162 *)b.delta, b.delta_s}, {(float2 *)b.psi, nullptr},
             rs, ss, (float)g->kappa, colour, nmr, nrhs, first_psi, gather, gather_only, d_err};
-        return dispatch_staging(g, a, s);
+        return dispatch_staging(g, a, s, pdl, timed);
     }
     default: break;
     }

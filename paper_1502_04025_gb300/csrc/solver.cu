@@ -230,8 +230,10 @@ qdd_status solve_impl(Gauge *g, Workspace *wsp, const double *b_in, double *x_ou
             if (p->use_sap) {
                 QDD_TRY(launch_spinor_convert(g, vj, nullptr, QDD_PREC_F64, w.rho.p, w.rho_s.as<float>(), sp, B, s));
                 sb.psi = zj;
+                SeqScope seq(ctx->timer, K_SAP, s);
                 for (int hs = 0; hs < 2 * p->ncy; hs++)
-                    QDD_TRY(launch_sap_halfsweep(g, sp, sb, hs & 1, p->nmr, B, hs < 2, hs >= 1, 0, w.err.as<int>(), s));
+                    QDD_TRY(launch_sap_halfsweep(g, sp, sb, hs & 1, p->nmr, B, hs < 2, hs >= 1, 0, w.err.as<int>(), s,
+                                                 hs >= 1, false));
             } else {
                 QDD_TRY(launch_spinor_convert(g, vj, nullptr, QDD_PREC_F64, zj, nullptr, zp, B, s));
             }
