@@ -119,6 +119,7 @@ def fgmres_dr(P: Problem, b, tol, m, k, max_cycles=100, state_hook=None):
         thetas.append(theta[:k].copy())
         Q, _ = np.linalg.qr(np.vstack([G[:, :k], np.zeros((1, k))]))
         q = rho - Q @ (Q.conj().T @ rho)
+        q = q - Q @ (Q.conj().T @ q)  # twice, for a tiny residual vector
         q = q / np.linalg.norm(q)
         Pk1 = np.hstack([Q, q[:, None]])
         Pk = Q[:m, :]
