@@ -552,7 +552,7 @@ def run_serve(args):
 
     pending = []          # (ticket, x) in submission order; x freed once polled
     lock = threading.Lock()
-    lat, ok, done = [], [0], threading.Event()
+    lat, ok, done, failures = [], [0], threading.Event(), []
 
     def poller():
         k = 0
@@ -566,6 +566,12 @@ def run_serve(args):
             if st == qdd.QDD_OK and rep["converged"]:
                 ok[0] += 1
                 lat.append(rep["seconds"])
+            else:
+                li, ki, r = reqs[k]
+                failures.append({"lattice": list(SERVE_LATTICES[li][0]), "kappa": SERVE_KAPPAS[ki], "nrhs": r,
+                                 "status": qdd.STATUS_NAMES[st] if 0 <= st < len(qdd.STATUS_NAMES) else st,
+                                 "error": qdd.qdd_last_error(),
+                                 "true_rel_res": rep["true_rel_res"] if rep else None})
             with lock:
                 pending[k] = None  # release the output buffer
             k += 1
@@ -592,7 +598,7 @@ def run_serve(args):
     line = {"metric": "SAP-FGMRES serving latency (submit to result)", "value": float(np.percentile(lat, 50)) * 1e3,
             "unit": "ms", "higher_is_better": False, "p50_ms": float(np.percentile(lat, 50)) * 1e3,
             "p99_ms": float(np.percentile(lat, 99)) * 1e3, "solves_per_s": ok / wall, "requests": n,
-            "converged": ok, "offered_rate_per_s": rate, "wall_s": wall, "data": "synthetic",
+            "converged": ok, "failures": failures, "offered_rate_per_s": rate, "wall_s": wall, "data": "synthetic",
             "config": {"workload": "serving mix: Poisson arrivals, lattices 8^4/16^3x32/24^3x48/32^3x64, "
                                    "kappa in {0.120,0.125,0.130,0.135}, 1-12 rhs, FP32 SAP, tol 1e-10",
                        "slots": 4, "hbm_budget_bytes": budget, "resident_gauge_bytes": used},

@@ -92,6 +92,11 @@ typedef struct {
                              error, e.g. 1e-6); 0 = off.  Needs an FP32
                              preconditioner output.  Convergence is still
                              decided on the FP64 true residual. */
+    int dr_k;             /* deflated restarts (Sec. 3.1: the outer solver is
+                             flexible GMRES with deflated restarts): keep the
+                             dr_k harmonic Ritz vectors of smallest modulus
+                             across each restart (0 = plain restarts;
+                             0 <= dr_k < restart_m). */
 } qdd_solve_params;
 
 typedef struct {
@@ -208,7 +213,7 @@ qdd_status qdd_sap_apply(qdd_gauge *g, const double *eta, double *psi, double *r
 
 /* Default parameters: tol 1e-10, m 16, 50 restarts, nmr 4, ncy 4, F32 SAP,
  * F64 Arnoldi operator, SAP on, 1 rhs, selective re-orthogonalisation,
- * no relaxation. */
+ * no relaxation, no deflation. */
 void qdd_default_params(qdd_solve_params *p);
 
 /*

@@ -566,6 +566,7 @@ void qdd_default_params(qdd_solve_params *p)
     p->nrhs = 1;
     p->reorth = 1;
     p->relax_eta = 0.0;
+    p->dr_k = 0;
 }
 
 qdd_status qdd_solve(qdd_gauge *g, const double *b, double *x, int on_device, const qdd_solve_params *p,

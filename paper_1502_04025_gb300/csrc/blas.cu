@@ -160,6 +160,35 @@ __global__ void __launch_bounds__(kBT) k_axpy_multi(const T2 *__restrict__ z, in
     }
 }
 
+// Basis recombination of a deflated restart: out_c (+)= sum_i src_i P[i][c]
+// for the NC columns c0..c0+NC-1 of P (row-major, ldp columns), src in FP64
+// or FP32, out in FP64.
+template <typename T2, int NC>
+__global__ void __launch_bounds__(kBT) k_combine(const T2 *__restrict__ src, int nsrc, int64_t ld,
+                                                 const double2 *__restrict__ P, int ldp, int c0, double2 *out,
+                                                 int64_t ldo, int64_t n, int accumulate)
+{
+    for (int64_t k = (int64_t)blockIdx.x * kBT + threadIdx.x; k < n; k += (int64_t)gridDim.x * kBT) {
+        double2 acc[NC];
+#pragma unroll
+        for (int c = 0; c < NC; c++) acc[c] = accumulate ? out[(int64_t)c * ldo + k] : make_double2(0, 0);
+        for (int i = 0; i < nsrc; i++) {
+            T2 a = src[i * ld + k];
+            double ax = (double)a.x, ay = (double)a.y;
+#pragma unroll
+            for (int c = 0; c < NC; c++) {
+                double2 p = __ldg(P + (int64_t)i * ldp + c0 + c);
+                acc[c].x = fma(p.x, ax, acc[c].x);
+                acc[c].x = fma(-p.y, ay, acc[c].x);
+                acc[c].y = fma(p.x, ay, acc[c].y);
+                acc[c].y = fma(p.y, ax, acc[c].y);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < NC; c++) out[(int64_t)c * ldo + k] = acc[c];
+    }
+}
+
 // ------------------------------------------------------------- launchers
 
 // Call f with std::integral_constant<int, NV> for NV = nv (1..kNV): kernels
@@ -249,6 +278,28 @@ qdd_status blas_scale_by_norm(Ctx *ctx, const double2 *w, int64_t n, const doubl
 {
     LaunchScope ls(ctx->timer, K_BLAS, s);
     k_scale_by_norm<<<blas_blocks(ctx, n), kBT, 0, s>>>(w, n, norm2, out);
+    QDD_CUDA(cudaGetLastError());
+    return QDD_OK;
+}
+
+qdd_status blas_combine(Ctx *ctx, const void *src, bool src_f32, int nsrc, int64_t ld, const double2 *P, int ldp,
+                        int ncols, double2 *out, int64_t ldo, int64_t n, int accumulate, cudaStream_t s)
+{
+    if (nsrc <= 0 || ncols <= 0) return QDD_OK;
+    const int nb = blas_blocks(ctx, n);
+    for (int c0 = 0; c0 < ncols; c0 += kNV) {
+        int nc = ncols - c0 < kNV ? ncols - c0 : kNV;
+        LaunchScope ls(ctx->timer, K_BLAS, s);
+        nv_dispatch(nc, [&](auto c) {
+            if (src_f32)
+                k_combine<float2, decltype(c)::value><<<nb, kBT, 0, s>>>((const float2 *)src, nsrc, ld, P, ldp, c0,
+                                                                         out + (int64_t)c0 * ldo, ldo, n, accumulate);
+            else
+                k_combine<double2, decltype(c)::value><<<nb, kBT, 0, s>>>((const double2 *)src, nsrc, ld, P, ldp, c0,
+                                                                          out + (int64_t)c0 * ldo, ldo, n,
+                                                                          accumulate);
+        });
+    }
     QDD_CUDA(cudaGetLastError());
     return QDD_OK;
 }

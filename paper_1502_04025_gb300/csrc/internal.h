@@ -166,6 +166,7 @@ struct Workspace {
     int nrhs = 0, m = 0;
     qdd_prec sp = QDD_PREC_F32;
     DevMem io, b, x, V, Z, rho, rho_s, delta, delta_s, dev, scratch, err;
+    DevMem ZR, Vt, ZRt, P;  // deflated restarts: recycled z (FP64), temporaries, P matrices
     double2 *host = nullptr;  // pinned mirror of `dev`
     size_t host_elems = 0;
     std::vector<double> hist;
@@ -257,10 +258,13 @@ qdd_status blas_scale_by_norm(Ctx *ctx, const double2 *w, int64_t n, const doubl
                               cudaStream_t s);
 qdd_status blas_axpy_multi(Ctx *ctx, const void *z, bool z_f32, int nvec, int64_t ld, const double2 *coef,
                            double2 *x, int64_t n, cudaStream_t s);
+// out_c (+)= sum_i src_i P[i*ldp + c], c < ncols (P on the device, row-major)
+qdd_status blas_combine(Ctx *ctx, const void *src, bool src_f32, int nsrc, int64_t ld, const double2 *P, int ldp,
+                        int ncols, double2 *out, int64_t ldo, int64_t n, int accumulate, cudaStream_t s);
 
 // solver.cu
 std::unique_ptr<Workspace> make_workspace();
-size_t workspace_bytes(const Gauge *g, int m, int nrhs, qdd_prec sp, bool use_sap);
+size_t workspace_bytes(const Gauge *g, int m, int nrhs, qdd_prec sp, bool use_sap, int kdr = 0);
 size_t workspace_held(const Workspace *w);
 void workspace_release(Workspace *w);
 // rel_out (optional): true relative residual of every right-hand side at return

@@ -39,7 +39,7 @@ static bool same_params(const qdd_solve_params &a, const qdd_solve_params &b)
 {
     return a.tol == b.tol && a.restart_m == b.restart_m && a.max_restarts == b.max_restarts && a.nmr == b.nmr &&
            a.ncy == b.ncy && a.sap_prec == b.sap_prec && a.arnoldi_prec == b.arnoldi_prec &&
-           a.use_sap == b.use_sap && a.reorth == b.reorth && a.relax_eta == b.relax_eta;
+           a.use_sap == b.use_sap && a.reorth == b.reorth && a.relax_eta == b.relax_eta && a.dr_k == b.dr_k;
 }
 
 static void worker_main(Ctx *ctx)
@@ -65,7 +65,7 @@ static void worker_main(Ctx *ctx)
                     // everything resident (this worker's own workspace is reused)
                     auto head = ctx->queue.front();
                     size_t need = workspace_bytes(head->g, head->p.restart_m, head->p.nrhs, head->p.sap_prec,
-                                                  head->p.use_sap != 0);
+                                                  head->p.use_sap != 0, head->p.dr_k);
                     size_t held = workspace_held(ws.get());
                     size_t used = ctx->used.load();
                     size_t others = used > held ? used - held : 0;
@@ -119,7 +119,7 @@ static void worker_main(Ctx *ctx)
         pm.nrhs = total;
         qdd_report rep{};
         std::vector<double> rel;
-        size_t need = workspace_bytes(batch[0]->g, pm.restart_m, total, pm.sap_prec, pm.use_sap != 0);
+        size_t need = workspace_bytes(batch[0]->g, pm.restart_m, total, pm.sap_prec, pm.use_sap != 0, pm.dr_k);
         if (workspace_held(ws.get()) > 2 * need) workspace_release(ws.get());
         clear_error();
         qdd_status s = single ? solve_impl(batch[0]->g, ws.get(), batch[0]->b.data(), batch[0]->x, 0, &pm, &rep, st,

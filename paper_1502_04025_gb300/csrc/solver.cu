@@ -1,7 +1,7 @@
-// Flexible GMRES(m), right-preconditioned by the Schwarz alternating procedure
-// (arXiv:1502.04025, Sec. 3.1: flexible GMRES outer solver, multiplicative
-// Schwarz preconditioner; the deflated restarts of the paper's solver are not
-// part of this form).
+// Flexible GMRES(m), right-preconditioned by the Schwarz alternating procedure,
+// optionally with deflated restarts (arXiv:1502.04025, Sec. 3.1: the outer
+// solver is flexible GMRES with deflated restarts, the preconditioner
+// multiplicative Schwarz).
 //
 //   x = 0; repeat:
 //     r = b - D x (FP64, true residual); stop when |r| <= tol |b|
@@ -13,8 +13,16 @@
 //                                                  re-orthogonalised when |w| drops
 //                                                  below |w_0|/sqrt(2), or always)
 //       h_{j+1,j} = |w|;  v_{j+1} = w / h_{j+1,j}
-//       Givens rotations on the host; |g_{j+1}| / |b| is the residual estimate
-//     y = R^{-1} g;  x += sum y_j z_j (FP64)
+//       min |c - Hbar y| on the host (Householder QR); its norm / |b| is the
+//       residual estimate
+//     x += sum y_j z_j (FP64)
+//   Deflated restart (dr_k = k > 0, after a full cycle): the k harmonic Ritz
+//   vectors g of smallest modulus (eigenvectors of H_m + H_m^{-H} l^H l, l the
+//   last row of Hbar) and the least-squares residual rho give an orthonormal
+//   P_{k+1}; V_{k+1} <- V_{m+1} P_{k+1}, Z_k <- Z_m P_k (kept in FP64),
+//   Hbar <- P_{k+1}^H Hbar P_k, c <- P_{k+1}^H rho, and the next cycle starts
+//   at step k.  If the true residual has drifted from the implicit one the
+//   restart falls back to the plain form.
 //
 // Right-hand sides are solved in lockstep: every kernel of a step handles all
 // of them (the Schwarz kernel reuses each staged domain for every source), the
@@ -26,6 +34,7 @@
 #include <cstring>
 
 #include "internal.h"
+#include "dense.h"
 
 namespace qdd {
 
@@ -48,7 +57,7 @@ struct ScalarMap {
 
 std::unique_ptr<Workspace> make_workspace() { return std::unique_ptr<Workspace>(new Workspace()); }
 
-size_t workspace_bytes(const Gauge *g, int m, int B, qdd_prec sp, bool use_sap)
+size_t workspace_bytes(const Gauge *g, int m, int B, qdd_prec sp, bool use_sap, int kdr)
 {
     const size_t V = g->hg.V, n = V * 12;
     const qdd_prec zp = sp == QDD_PREC_F64 ? QDD_PREC_F64 : QDD_PREC_F32;
@@ -57,13 +66,14 @@ size_t workspace_bytes(const Gauge *g, int m, int B, qdd_prec sp, bool use_sap)
         b += 2 * n * ebytes(sp) * B;
         if (sp == QDD_PREC_F16S || sp == QDD_PREC_BF16S) b += 2 * V * 4 * B;
     }
+    if (kdr > 0) b += n * 16 * B * (size_t)(3 * kdr + 1);
     return b + (1 << 20);
 }
 
 size_t workspace_held(const Workspace *w)
 {
     const DevMem *all[] = {&w->io, &w->b, &w->x, &w->V, &w->Z, &w->rho, &w->rho_s, &w->delta, &w->delta_s,
-                           &w->dev, &w->scratch, &w->err};
+                           &w->dev, &w->scratch, &w->err, &w->ZR, &w->Vt, &w->ZRt, &w->P};
     size_t t = 0;
     for (auto *d : all) t += d->bytes;
     return t;
@@ -72,11 +82,11 @@ size_t workspace_held(const Workspace *w)
 void workspace_release(Workspace *w)
 {
     DevMem *all[] = {&w->io, &w->b, &w->x, &w->V, &w->Z, &w->rho, &w->rho_s, &w->delta, &w->delta_s,
-                     &w->dev, &w->scratch, &w->err};
+                     &w->dev, &w->scratch, &w->err, &w->ZR, &w->Vt, &w->ZRt, &w->P};
     for (auto *d : all) d->release();
 }
 
-static qdd_status ensure_ws(Gauge *g, Workspace &w, int m, int B, qdd_prec sp, bool use_sap)
+static qdd_status ensure_ws(Gauge *g, Workspace &w, int m, int B, qdd_prec sp, bool use_sap, int kdr)
 {
     Ctx *c = g->ctx;
     const size_t V = g->hg.V, n = V * 12;
@@ -93,6 +103,12 @@ static qdd_status ensure_ws(Gauge *g, Workspace &w, int m, int B, qdd_prec sp, b
             QDD_TRY(w.rho_s.ensure(c, V * 4 * B));
             QDD_TRY(w.delta_s.ensure(c, V * 4 * B));
         }
+    }
+    if (kdr > 0) {
+        QDD_TRY(w.ZR.ensure(c, n * 16 * B * (size_t)kdr));
+        QDD_TRY(w.ZRt.ensure(c, n * 16 * B * (size_t)kdr));
+        QDD_TRY(w.Vt.ensure(c, n * 16 * B * (size_t)(kdr + 1)));
+        QDD_TRY(w.P.ensure(c, sizeof(double2) * B * (size_t)(m + 1) * (kdr + 1)));
     }
     ScalarMap sm{m, B};
     QDD_TRY(w.dev.ensure(c, sm.total() * sizeof(double2)));
@@ -119,7 +135,7 @@ qdd_status solve_impl(Gauge *g, Workspace *wsp, const double *b_in, double *x_ou
     if (m < 1 || m > 64 || B < 1 || B > 64 || !(p->tol > 0) || p->max_restarts < 0 || p->nmr < 0 || p->ncy < 1 ||
         p->sap_prec < QDD_PREC_F64 || p->sap_prec > QDD_PREC_BF16S ||
         (p->arnoldi_prec != QDD_PREC_F64 && p->arnoldi_prec != QDD_PREC_F32 && p->arnoldi_prec != QDD_PREC_DF64) ||
-        p->reorth < 0 || p->reorth > 2) {
+        p->reorth < 0 || p->reorth > 2 || p->dr_k < 0 || p->dr_k >= m) {
         set_error("invalid solve parameters");
         return QDD_EINVAL;
     }
@@ -138,7 +154,7 @@ qdd_status solve_impl(Gauge *g, Workspace *wsp, const double *b_in, double *x_ou
         return QDD_EINVAL;
     }
     Workspace &w = *wsp;
-    QDD_TRY(ensure_ws(g, w, m, B, sp, p->use_sap != 0));
+    QDD_TRY(ensure_ws(g, w, m, B, sp, p->use_sap != 0, p->dr_k));
     if (p->use_sap) QDD_TRY(ensure_copy(g, sp, s));
     if (p->arnoldi_prec != QDD_PREC_F64) QDD_TRY(ensure_copy(g, p->arnoldi_prec, s));
     if (p->relax_eta > 0) QDD_TRY(ensure_copy(g, QDD_PREC_F32, s));
@@ -176,24 +192,30 @@ qdd_status solve_impl(Gauge *g, Workspace *wsp, const double *b_in, double *x_ou
 
     std::vector<char> active(B, 1);
     std::vector<double> rel(B, 0.0), est(B, 0.0);
-    std::vector<std::vector<zc>> H(B, std::vector<zc>((size_t)(m + 1) * m)), gv(B, std::vector<zc>(m + 1));
-    std::vector<std::vector<double>> cs(B, std::vector<double>(m));
-    std::vector<std::vector<zc>> sn(B, std::vector<zc>(m));
+    // per rhs: Hbar (m+1) x m, right-hand side c of the small least-squares
+    // problem, the columns of this cycle, the recycled count j0
+    std::vector<dense::Mat> H(B, dense::Mat(m + 1, m));
+    std::vector<std::vector<zc>> cv(B, std::vector<zc>(m + 1)), rho(B);
     std::vector<int> kr(B, 0);
+    int j0 = 0;                  // columns carried over by a deflated restart (same for all rhs)
+    bool pending_dr = false;     // the previous cycle ended ready for a deflated restart
+    const int kdr = p->dr_k;
     w.hist.clear();
     int iters = 0, restarts = 0;
     bool converged = false;
     qdd_status status = QDD_OK;
     SapBuffers sb{w.rho.p, w.delta.p, nullptr, w.rho_s.as<float>(), w.delta_s.as<float>()};
+    double2 *ZR = w.ZR.as<double2>();
 
     for (int cycle = 0;; cycle++) {
-        // ---- true residual into V_0
+        // ---- true residual into V_0 (FP64)
         if (cycle == 0)
             QDD_CUDA(cudaMemcpyAsync(V, Bv, (size_t)n * 16 * B, cudaMemcpyDeviceToDevice, s));
         else
-            QDD_TRY(launch_dslash(g, QDD_PREC_F64, QDD_PREC_F64, X, nullptr, QDD_PREC_F64, V, nullptr, QDD_PREC_F64,
-                                  Bv, B, s));
-        for (int r = 0; r < B; r++) QDD_TRY(blas_norm2(ctx, V + r * n, n, dev + sm.nrm1() + r, scr, s));
+            QDD_TRY(launch_dslash(g, QDD_PREC_F64, QDD_PREC_F64, X, nullptr, QDD_PREC_F64, pending_dr ? w.Vt.as<double2>() : V,
+                                  nullptr, QDD_PREC_F64, Bv, B, s));
+        double2 *R0 = (cycle > 0 && pending_dr) ? w.Vt.as<double2>() : V;
+        for (int r = 0; r < B; r++) QDD_TRY(blas_norm2(ctx, R0 + r * n, n, dev + sm.nrm1() + r, scr, s));
         QDD_CUDA(cudaMemcpyAsync(host + sm.nrm1(), dev + sm.nrm1(), B * sizeof(double2), cudaMemcpyDeviceToHost, s));
         QDD_CUDA(cudaStreamSynchronize(s));
         bool all = true;
@@ -206,9 +228,6 @@ qdd_status solve_impl(Gauge *g, Workspace *wsp, const double *b_in, double *x_ou
             rel[r] = bnorm[r] > 0 ? beta / bnorm[r] : 0.0;
             if (rel[r] <= p->tol) active[r] = 0;
             all = all && !active[r];
-            gv[r].assign(m + 1, zc(0, 0));
-            gv[r][0] = beta;
-            kr[r] = 0;
         }
         if (cycle > 0) w.hist.push_back(rel[0]);
         if (status != QDD_OK) break;
@@ -217,12 +236,129 @@ qdd_status solve_impl(Gauge *g, Workspace *wsp, const double *b_in, double *x_ou
             break;
         }
         if (cycle > p->max_restarts) break;
-        for (int r = 0; r < B; r++) QDD_TRY(blas_scale_by_norm(ctx, V + r * n, n, dev + sm.nrm1() + r, V + r * n, s));
-        for (int r = 0; r < B; r++) std::fill(H[r].begin(), H[r].end(), zc(0, 0));
+
+        // ---- deflated restart (harmonic Ritz vectors of the last cycle), else plain restart
+        bool deflate = pending_dr;
+        std::vector<dense::Mat> Pm(B);
+        if (deflate) {
+            for (int r = 0; r < B && deflate; r++) {
+                if (!active[r]) continue;
+                // the implicit residual must still describe the true one
+                double implicit = dense::nrm(rho[r]);
+                double truth = rel[r] * bnorm[r];
+                if (!(truth <= 2.0 * implicit + 1e-300)) { deflate = false; break; }
+                const dense::Mat &Hb = H[r];
+                dense::Mat Hm(m, m), rhs(m, m);
+                for (int i = 0; i < m; i++)
+                    for (int jj = 0; jj < m; jj++) Hm(i, jj) = Hb(i, jj);
+                // F = H_m + H_m^{-H} l^H l, l = last row of Hbar
+                dense::Mat HmH(m, m);
+                for (int i = 0; i < m; i++)
+                    for (int jj = 0; jj < m; jj++) {
+                        HmH(i, jj) = std::conj(Hm(jj, i));
+                        rhs(i, jj) = std::conj(Hb(m, i)) * Hb(m, jj);
+                    }
+                if (!dense::solve(HmH, rhs)) { deflate = false; break; }
+                dense::Mat F(m, m);
+                for (size_t t = 0; t < F.a.size(); t++) F.a[t] = Hm.a[t] + rhs.a[t];
+                std::vector<zc> theta;
+                dense::Mat G;
+                if (!dense::eig(F, theta, G)) { deflate = false; break; }
+                std::vector<int> ord(m);
+                for (int i = 0; i < m; i++) ord[i] = i;
+                std::stable_sort(ord.begin(), ord.end(),
+                                 [&](int x, int y) { return std::abs(theta[x]) < std::abs(theta[y]); });
+                dense::Mat Gk(m + 1, kdr);
+                for (int c = 0; c < kdr; c++)
+                    for (int i = 0; i < m; i++) Gk(i, c) = G(i, ord[c]);
+                dense::Mat Q = dense::orthonormal(Gk);
+                // last column: the least-squares residual, orthogonalised twice
+                dense::Mat P(m + 1, kdr + 1);
+                for (int i = 0; i <= m; i++)
+                    for (int c = 0; c < kdr; c++) P(i, c) = Q(i, c);
+                std::vector<zc> q = rho[r];
+                for (int pass = 0; pass < 2; pass++)
+                    for (int c = 0; c < kdr; c++) {
+                        zc sc = 0;
+                        for (int i = 0; i <= m; i++) sc += std::conj(Q(i, c)) * q[i];
+                        for (int i = 0; i <= m; i++) q[i] -= sc * Q(i, c);
+                    }
+                double qn = dense::nrm(q);
+                if (!(qn > 0)) { deflate = false; break; }
+                for (int i = 0; i <= m; i++) P(i, kdr) = q[i] / qn;
+                Pm[r] = P;
+            }
+        }
+        if (deflate) {
+            // upload P (row-major (m+1) x (kdr+1) per rhs), recombine V and Z on the device
+            double2 *Pd = w.P.as<double2>();
+            std::vector<double2> ph((size_t)B * (m + 1) * (kdr + 1), make_double2(0, 0));
+            for (int r = 0; r < B; r++) {
+                if (!active[r]) continue;
+                for (int i = 0; i <= m; i++)
+                    for (int c = 0; c <= kdr; c++) {
+                        zc v = Pm[r](i, c);
+                        ph[((size_t)r * (m + 1) + i) * (kdr + 1) + c] = make_double2(v.real(), v.imag());
+                    }
+            }
+            QDD_CUDA(cudaMemcpyAsync(Pd, ph.data(), ph.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
+            double2 *Vt = w.Vt.as<double2>(), *ZRt = w.ZRt.as<double2>();
+            for (int r = 0; r < B; r++) {
+                if (!active[r]) continue;
+                const double2 *Pr = Pd + (size_t)r * (m + 1) * (kdr + 1);
+                // V_new[c] = sum_{i<=m} V_i P[i][c], c <= kdr
+                QDD_TRY(blas_combine(ctx, V + r * n, false, m + 1, ldV, Pr, kdr + 1, kdr + 1, Vt + r * n, n * B, n,
+                                     0, s));
+                // Z_new[c] = sum_{i<j0} ZR_i P[i][c] + sum_{i=j0..m-1} Z_i P[i][c], c < kdr
+                if (j0 > 0)
+                    QDD_TRY(blas_combine(ctx, ZR + r * n, false, j0, ldV, Pr, kdr + 1, kdr, ZRt + r * n, n * B, n, 0,
+                                         s));
+                QDD_TRY(blas_combine(ctx, Z + ((size_t)j0 * n * B + r * n) * zb, zp == QDD_PREC_F32, m - j0,
+                                     (int64_t)n * B, Pr + (size_t)j0 * (kdr + 1), kdr + 1, kdr, ZRt + r * n, n * B, n,
+                                     j0 > 0 ? 1 : 0, s));
+            }
+            QDD_CUDA(cudaMemcpyAsync(V, Vt, (size_t)(kdr + 1) * n * 16 * B, cudaMemcpyDeviceToDevice, s));
+            QDD_CUDA(cudaMemcpyAsync(ZR, ZRt, (size_t)kdr * n * 16 * B, cudaMemcpyDeviceToDevice, s));
+            for (int r = 0; r < B; r++) {
+                if (!active[r]) continue;
+                const dense::Mat &P = Pm[r];
+                dense::Mat Hn(m + 1, m);
+                std::vector<zc> cn(m + 1, zc(0, 0));
+                // Hbar_new = P^H Hbar P_k ; c_new = P^H rho
+                for (int a2 = 0; a2 <= kdr; a2++) {
+                    for (int b2 = 0; b2 < kdr; b2++) {
+                        zc sum = 0;
+                        for (int i = 0; i <= m; i++)
+                            for (int jj = 0; jj < m; jj++)
+                                sum += std::conj(P(i, a2)) * H[r](i, jj) * P(jj, b2);
+                        Hn(a2, b2) = sum;
+                    }
+                    zc sum = 0;
+                    for (int i = 0; i <= m; i++) sum += std::conj(P(i, a2)) * rho[r][i];
+                    cn[a2] = sum;
+                }
+                H[r] = Hn;
+                cv[r] = cn;
+                kr[r] = kdr;
+            }
+            j0 = kdr;
+            restarts++;
+        } else {
+            for (int r = 0; r < B; r++)
+                QDD_TRY(blas_scale_by_norm(ctx, R0 + r * n, n, dev + sm.nrm1() + r, V + r * n, s));
+            for (int r = 0; r < B; r++) {
+                H[r] = dense::Mat(m + 1, m);
+                cv[r].assign(m + 1, zc(0, 0));
+                cv[r][0] = rel[r] * bnorm[r];
+                kr[r] = 0;
+            }
+            if (cycle > 0) restarts++;
+            j0 = 0;
+        }
+        pending_dr = false;
 
         std::vector<char> open(active);  // still iterating in this cycle
-        int kmax = 0;
-        for (int j = 0; j < m; j++) {
+        for (int j = j0; j < m; j++) {
             double2 *vj = V + (int64_t)j * ldV;
             double2 *wv = V + (int64_t)(j + 1) * ldV;
             char *zj = Z + (size_t)j * n * B * zb;
@@ -242,7 +378,7 @@ qdd_status solve_impl(Gauge *g, Workspace *wsp, const double *b_in, double *x_ou
             // accuracy (inexact Krylov: error allowed ~ tol / residual)
             double est_now = 0;
             for (int r = 0; r < B; r++)
-                if (open[r]) est_now = std::max(est_now, j == 0 ? rel[r] : est[r]);
+                if (open[r]) est_now = std::max(est_now, j == j0 ? rel[r] : est[r]);
             const bool relaxed = p->relax_eta > 0 && p->relax_eta * est_now <= 0.1 * p->tol;
             if (relaxed)
                 QDD_TRY(launch_dslash(g, QDD_PREC_F32, QDD_PREC_F32, zj, nullptr, QDD_PREC_F32, wv, nullptr,
@@ -298,7 +434,7 @@ qdd_status solve_impl(Gauge *g, Workspace *wsp, const double *b_in, double *x_ou
             bool all_done = true;
             for (int r = 0; r < B; r++) {
                 if (!open[r]) continue;
-                std::vector<zc> &h = H[r];
+                dense::Mat &h = H[r];
                 for (int i = 0; i <= j; i++) {
                     double2 a = host[sm.dots1() + (size_t)r * (m + 2) + i];
                     zc hij(a.x, a.y);
@@ -306,7 +442,7 @@ qdd_status solve_impl(Gauge *g, Workspace *wsp, const double *b_in, double *x_ou
                         double2 c2 = host[sm.dots2() + (size_t)r * (m + 2) + i];
                         hij += zc(c2.x, c2.y);
                     }
-                    h[(size_t)i * m + j] = hij;
+                    h(i, j) = hij;
                 }
                 double nn = two[r] ? host[sm.nrm2() + r].x : host[sm.nrm1() + r].x;
                 double hn = std::sqrt(nn);
@@ -314,64 +450,50 @@ qdd_status solve_impl(Gauge *g, Workspace *wsp, const double *b_in, double *x_ou
                     set_error("non-finite Arnoldi norm (rhs %d, step %d)", r, j);
                     status = QDD_ENAN;
                 }
-                h[(size_t)(j + 1) * m + j] = hn;
+                h(j + 1, j) = hn;
                 // v_{j+1} = w / h_{j+1,j}
                 QDD_TRY(blas_scale_by_norm(ctx, wv + r * n, n, dev + (two[r] ? sm.nrm2() : sm.nrm1()) + r, wv + r * n,
                                            s));
-                // rotations
-                for (int i = 0; i < j; i++) {
-                    zc a = h[(size_t)i * m + j], c2 = h[(size_t)(i + 1) * m + j];
-                    h[(size_t)i * m + j] = cs[r][i] * a + sn[r][i] * c2;
-                    h[(size_t)(i + 1) * m + j] = -std::conj(sn[r][i]) * a + cs[r][i] * c2;
-                }
-                zc a = h[(size_t)j * m + j], bb = h[(size_t)(j + 1) * m + j];
-                double nu = std::sqrt(std::norm(a) + std::norm(bb));
-                if (std::abs(a) == 0.0) {
-                    cs[r][j] = 0.0;
-                    sn[r][j] = 1.0;
-                    h[(size_t)j * m + j] = bb;
-                } else {
-                    zc ph = a / std::abs(a);
-                    cs[r][j] = std::abs(a) / nu;
-                    sn[r][j] = ph * std::conj(bb) / nu;
-                    h[(size_t)j * m + j] = ph * nu;
-                }
-                h[(size_t)(j + 1) * m + j] = 0;
-                gv[r][j + 1] = -std::conj(sn[r][j]) * gv[r][j];
-                gv[r][j] = cs[r][j] * gv[r][j];
+                // residual estimate: min |c - Hbar y| over the j+1 columns
+                dense::Mat Hs(j + 2, j + 1);
+                for (int i = 0; i < j + 2; i++)
+                    for (int l = 0; l < j + 1; l++) Hs(i, l) = h(i, l);
+                std::vector<zc> cs(cv[r].begin(), cv[r].begin() + j + 2), y, res;
+                dense::lstsq(Hs, cs, y, res);
                 kr[r] = j + 1;
-                est[r] = bnorm[r] > 0 ? std::abs(gv[r][j + 1]) / bnorm[r] : 0.0;
+                est[r] = bnorm[r] > 0 ? dense::nrm(res) / bnorm[r] : 0.0;
                 if (r == 0) w.hist.push_back(est[0]);
                 if (est[r] <= p->tol || hn == 0.0) open[r] = 0;
                 all_done = all_done && !open[r];
             }
-            kmax = j + 1;
             if (status != QDD_OK || all_done) break;
         }
         if (status != QDD_OK) break;
-        // x += Z y per rhs
+        // x += Z y per rhs (recycled z in FP64, the rest in the preconditioner's precision)
+        bool full = true;
         for (int r = 0; r < B; r++) {
             if (!active[r] || kr[r] == 0) continue;
             int k = kr[r];
-            std::vector<zc> y(k);
-            const std::vector<zc> &h = H[r];
-            for (int i = k - 1; i >= 0; i--) {
-                zc acc = gv[r][i];
-                for (int l = i + 1; l < k; l++) acc -= h[(size_t)i * m + l] * y[l];
-                y[i] = acc / h[(size_t)i * m + i];
-            }
+            dense::Mat Hs(k + 1, k);
+            for (int i = 0; i <= k; i++)
+                for (int l = 0; l < k; l++) Hs(i, l) = H[r](i, l);
+            std::vector<zc> cs(cv[r].begin(), cv[r].begin() + k + 1), y;
+            dense::lstsq(Hs, cs, y, rho[r]);
+            rho[r].resize(m + 1, zc(0, 0));
             double2 *cf = host + sm.coef() + (size_t)r * (m + 1);
             for (int i = 0; i < k; i++) cf[i] = make_double2(y[i].real(), y[i].imag());
+            full = full && k == m;
         }
         QDD_CUDA(cudaMemcpyAsync(dev + sm.coef(), host + sm.coef(), (size_t)B * (m + 1) * sizeof(double2),
                                  cudaMemcpyHostToDevice, s));
         for (int r = 0; r < B; r++) {
             if (!active[r] || kr[r] == 0) continue;
-            QDD_TRY(blas_axpy_multi(ctx, Z + (size_t)r * n * zb, zp == QDD_PREC_F32, kr[r], n * B,
-                                    dev + sm.coef() + (size_t)r * (m + 1), X + r * n, n, s));
+            const double2 *cf = dev + sm.coef() + (size_t)r * (m + 1);
+            if (j0 > 0) QDD_TRY(blas_axpy_multi(ctx, ZR + r * n, false, j0, n * B, cf, X + r * n, n, s));
+            QDD_TRY(blas_axpy_multi(ctx, Z + ((size_t)j0 * n * B + r * n) * zb, zp == QDD_PREC_F32, kr[r] - j0,
+                                    n * B, cf + j0, X + r * n, n, s));
         }
-        (void)kmax;
-        restarts = cycle;
+        pending_dr = kdr > 0 && full;
     }
 
     // ---- output

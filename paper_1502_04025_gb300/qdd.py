@@ -33,7 +33,7 @@ class qdd_solve_params(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("restart_m", ctypes.c_int), ("max_restarts", ctypes.c_int),
                 ("nmr", ctypes.c_int), ("ncy", ctypes.c_int), ("sap_prec", ctypes.c_int),
                 ("arnoldi_prec", ctypes.c_int), ("use_sap", ctypes.c_int), ("nrhs", ctypes.c_int),
-                ("reorth", ctypes.c_int), ("relax_eta", ctypes.c_double)]
+                ("reorth", ctypes.c_int), ("relax_eta", ctypes.c_double), ("dr_k", ctypes.c_int)]
 
 
 class qdd_report(ctypes.Structure):

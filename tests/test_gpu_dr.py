@@ -1,0 +1,71 @@
+"""GPU FGMRES with deflated restarts against the reference (oracle/fgmres_dr.py)
+and against plain restarted FGMRES on the same system."""
+import numpy as np
+import pytest
+
+from paper_1502_04025_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+L44, DOM2 = (4, 4, 4, 4), (2, 2, 2, 2)
+
+
+@pytest.fixture(scope="module")
+def q():
+    from paper_1502_04025_gb300 import build
+
+    build.build()
+    from paper_1502_04025_gb300 import qdd
+
+    return qdd
+
+
+@pytest.fixture(scope="module")
+def setup(q, ora):
+    from oracle import fgmres_dr as dr
+
+    U = inputs.gauge_field(L44, 0.5, 1001)
+    kappa = 0.13
+    A = ora.clover(L44, U, 1.0, kappa)
+    Ainv = ora.invert_clover(L44, A)
+    ctx = q.qdd_create(0, 0)
+    g = q.qdd_create_gauge_field(ctx, L44, DOM2, U)
+    q.qdd_set_clover(g, 1.0, kappa)
+    return dict(dr=dr, U=U, A=A, Ainv=Ainv, kappa=kappa, ctx=ctx, g=g)
+
+
+def _rel_res(ora, S, x, b):
+    r = b - ora.apply_D(L44, S["U"], S["A"], S["kappa"], x)
+    return np.linalg.norm(r) / np.linalg.norm(b)
+
+
+def test_dr_matches_reference_and_beats_plain_restarts(q, ora, setup):
+    S = setup
+    b = inputs.gaussian_source(L44, 2301)
+    P = S["dr"].Problem(L44, DOM2, S["U"], S["A"], S["Ainv"], S["kappa"], use_sap=False)
+    x_o, info = S["dr"].fgmres_dr(P, b.reshape(-1), 1e-11, m=10, k=5, max_cycles=200)
+    assert info["converged"]
+    common = dict(tol=1e-11, restart_m=10, use_sap=0, sap_prec="f64", arnoldi_prec="f64", max_restarts=300, reorth=2)
+    x_dr, r_dr = q.qdd_solve(S["g"], b, dr_k=5, **common)
+    x_pl, r_pl = q.qdd_solve(S["g"], b, dr_k=0, **common)
+    assert r_dr["converged"] and r_pl["converged"]
+    assert _rel_res(ora, S, x_dr, b) <= 1e-11
+    assert abs(r_dr["iters"] - info["iters"]) <= max(3, info["iters"] // 10)
+    assert r_dr["iters"] < r_pl["iters"]
+    assert np.linalg.norm(x_dr - x_o.reshape(b.shape)) <= 1e-8 * np.linalg.norm(x_o)
+
+
+def test_dr_with_the_schwarz_preconditioner(q, ora, setup):
+    S = setup
+    b = inputs.gaussian_source(L44, 2302)
+    for prec in ("f64", "f32"):
+        x, rep = q.qdd_solve(S["g"], b, tol=1e-10, restart_m=4, dr_k=2, sap_prec=prec, nmr=1, ncy=1,
+                             max_restarts=200)
+        assert rep["converged"]
+        assert _rel_res(ora, S, x, b) <= 1e-10
+
+
+def test_dr_parameter_checks(q, setup):
+    b = inputs.gaussian_source(L44, 2303)
+    with pytest.raises(q.QddError):
+        q.qdd_solve(setup["g"], b, restart_m=4, dr_k=4)
