@@ -67,9 +67,11 @@ typedef enum {
     QDD_PREC_F32 = 1,
     QDD_PREC_F16S = 2,
     QDD_PREC_BF16S = 3,
-    QDD_PREC_DF64 = 4 /* operator only: FP64-class accuracy (about 2^-46) from
-                         pairs of FP32 numbers; links and clover split into
-                         hi + lo parts.  For qdd_apply_D and arnoldi_prec. */
+    QDD_PREC_DF64 = 4, /* operator only: FP64-class accuracy (about 2^-46) from
+                          pairs of FP32 numbers; links and clover split into
+                          hi + lo parts.  For qdd_apply_D and arnoldi_prec. */
+    QDD_PREC_H16 = 5   /* the paper's half precision (Sec. 3.3): FP16 links and
+                          clover (per-site scale), FP32 spinors, FP32 arithmetic */
 } qdd_prec;
 
 typedef struct {
@@ -111,6 +113,7 @@ typedef struct {
     double ms_blas;         /* device time in FP64 vector kernels */
     long long sap_launches; /* Schwarz block-kernel launches */
     long long kernel_launches; /* all kernel launches of the call */
+    int deflated_restarts;  /* restarts that kept harmonic Ritz vectors (dr_k > 0) */
     int n_history;          /* entries of res_history */
     const double *res_history; /* estimated relative residual per iteration of
                                   rhs 0, and the true one at each restart;

@@ -153,6 +153,7 @@ static size_t elem_bytes(qdd_prec p)
 qdd_status ensure_copy(Gauge *g, qdd_prec prec, cudaStream_t s)
 {
     if (prec == QDD_PREC_F64) return QDD_OK;
+    if (prec == QDD_PREC_H16) return ensure_copy(g, QDD_PREC_F16S, s);
     if (prec < QDD_PREC_F64 || prec > QDD_PREC_DF64) {
         set_error("invalid precision %d", (int)prec);
         return QDD_EINVAL;
@@ -461,7 +462,7 @@ qdd_status qdd_apply_D(qdd_gauge *g, const double *in, double *out, int nrhs, qd
                        void *stream)
 {
     clear_error();
-    if (!g || !in || !out || nrhs < 1 || prec < QDD_PREC_F64 || prec > QDD_PREC_DF64) {
+    if (!g || !in || !out || nrhs < 1 || prec < QDD_PREC_F64 || prec > QDD_PREC_H16) {
         set_error("invalid argument");
         return QDD_EINVAL;
     }
@@ -472,11 +473,12 @@ qdd_status qdd_apply_D(qdd_gauge *g, const double *in, double *out, int nrhs, qd
     auto &st = stg[g];
     if (!st) st.reset(new Staging());
     const size_t V = g->hg.V;
-    const size_t eb = elem_bytes(prec);
+    const size_t eb = elem_bytes(spinor_store(prec));
     const bool scaled = prec == QDD_PREC_F16S || prec == QDD_PREC_BF16S;
     const qdd_prec arith = prec == QDD_PREC_F64 || prec == QDD_PREC_DF64 ? prec : QDD_PREC_F32;
-    const qdd_prec fp = prec;                                             // link / clover copy
+    const qdd_prec fp = field_store(prec);                                // link / clover copy
     if (prec == QDD_PREC_DF64) prec = QDD_PREC_F64;                       // spinor storage
+    prec = spinor_store(prec);
     const double *din = nullptr;
     double *dout = nullptr;
     QDD_TRY(stage_in(g, st->io, in, nrhs, on_device, s, &din));
@@ -498,7 +500,7 @@ qdd_status qdd_sap_apply(qdd_gauge *g, const double *eta, double *psi, double *r
                          qdd_prec prec, int on_device, void *stream)
 {
     clear_error();
-    if (!g || !eta || !psi || nrhs < 1 || nmr < 0 || n_half < 1 || prec < QDD_PREC_F64 || prec > QDD_PREC_BF16S) {
+    if (!g || !eta || !psi || nrhs < 1 || nmr < 0 || n_half < 1 || !is_sap_prec(prec)) {
         set_error("invalid argument");
         return QDD_EINVAL;
     }
@@ -509,7 +511,8 @@ qdd_status qdd_sap_apply(qdd_gauge *g, const double *eta, double *psi, double *r
     auto &st = stg[g];
     if (!st) st.reset(new Staging());
     const size_t V = g->hg.V;
-    const size_t eb = elem_bytes(prec);
+    const qdd_prec ssp = spinor_store(prec);                                 // rho, delta storage
+    const size_t eb = elem_bytes(ssp);
     const qdd_prec pp = prec == QDD_PREC_F64 ? QDD_PREC_F64 : QDD_PREC_F32;  // psi storage
     const bool scaled = prec == QDD_PREC_F16S || prec == QDD_PREC_BF16S;
     const double *din = nullptr;
@@ -523,7 +526,7 @@ qdd_status qdd_sap_apply(qdd_gauge *g, const double *eta, double *psi, double *r
         QDD_TRY(st->b_s.ensure(g->ctx, V * 4 * nrhs));
     }
     QDD_CUDA(cudaMemsetAsync(st->err.p, 0, sizeof(int), s));
-    QDD_TRY(launch_spinor_in(g, din, st->a.p, st->a_s.as<float>(), prec, nrhs, s));
+    QDD_TRY(launch_spinor_in(g, din, st->a.p, st->a_s.as<float>(), ssp, nrhs, s));
     if (n_half < 2) QDD_CUDA(cudaMemsetAsync(st->c.p, 0, V * 12 * elem_bytes(pp) * nrhs, s));
     SapBuffers b{st->a.p, st->b.p, st->c.p, st->a_s.as<float>(), st->b_s.as<float>()};
     {
@@ -540,7 +543,7 @@ qdd_status qdd_sap_apply(qdd_gauge *g, const double *eta, double *psi, double *r
     QDD_TRY(finish_out(g, st->io, psi, nrhs, on_device, s));
     if (rho) {
         QDD_TRY(stage_out(g, st->io, rho, nrhs, on_device, s, &dout));
-        QDD_TRY(launch_spinor_out(g, st->a.p, st->a_s.as<float>(), dout, prec, nrhs, s));
+        QDD_TRY(launch_spinor_out(g, st->a.p, st->a_s.as<float>(), dout, ssp, nrhs, s));
         QDD_TRY(finish_out(g, st->io, rho, nrhs, on_device, s));
     }
     int err = 0;

@@ -344,6 +344,9 @@ qdd_status launch_dslash(Gauge *g, qdd_prec arith, qdd_prec fp, const void *in, 
             if (ip == QDD_PREC_F16S && op == QDD_PREC_F16S)
                 return run_dslash<float, StF16, StF16, StF16, StF16, false>(g, U, A, in, in_s, out, out_s, b, nrhs,
                                                                             s);
+            if (ip == QDD_PREC_F32 && op == QDD_PREC_F32)  // half links/clover, single spinors
+                return run_dslash<float, StF16, StF16, StF32, StF32, false>(g, U, A, in, in_s, out, out_s, b, nrhs,
+                                                                            s);
             break;
         }
         case QDD_PREC_BF16S: {

@@ -201,6 +201,14 @@ struct Fields {
 
 qdd_status ensure_copy(Gauge *g, qdd_prec prec, cudaStream_t s);
 
+// storage of the spinors and of the links/clover copy a precision mode uses
+inline qdd_prec spinor_store(qdd_prec p) { return p == QDD_PREC_H16 ? QDD_PREC_F32 : p; }
+inline qdd_prec field_store(qdd_prec p) { return p == QDD_PREC_H16 ? QDD_PREC_F16S : p; }
+inline bool is_sap_prec(qdd_prec p)
+{
+    return p == QDD_PREC_F64 || p == QDD_PREC_F32 || p == QDD_PREC_F16S || p == QDD_PREC_BF16S || p == QDD_PREC_H16;
+}
+
 // ------------------------------------------------------------- launchers
 
 // layout.cu

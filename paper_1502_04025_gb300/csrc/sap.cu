@@ -1096,6 +1096,7 @@ size_t sap_smem_bytes(const HostGeom &hg, qdd_prec prec, bool stl, bool stc)
     case QDD_PREC_F64: return sap_smem_layout<double, StF64, StF64>(hg.Vd, stl, stc);
     case QDD_PREC_F32: return sap_smem_layout<float, StF32, StF32>(hg.Vd, stl, stc);
     case QDD_PREC_F16S: return sap_smem_layout<float, StF16, StF16>(hg.Vd, stl, stc);
+    case QDD_PREC_H16: return sap_smem_layout<float, StF16, StF16>(hg.Vd, stl, stc);
     default: return sap_smem_layout<float, StBF16, StBF16>(hg.Vd, stl, stc);
     }
 }
@@ -1126,6 +1127,14 @@ qdd_status launch_sap_halfsweep(Gauge *g, qdd_prec prec, const SapBuffers &b, in
         SapArgs<float, StF16, StF16, StF16, StF32> a{
             g->geom, {c.links.as<__half2>(), nullptr}, {c.sclov.as<__half2>(), c.sclov_s.as<float>()},
             {(__half2 *)b.rho, b.rho_s}, {(__half2 *)b.delta, b.delta_s}, {(float2 *)b.psi, nullptr},
+            rs, ss, (float)g->kappa, colour, nmr, nrhs, first_psi, gather, gather_only, d_err};
+        return dispatch_staging(g, a, s, pdl, timed);
+    }
+    case QDD_PREC_H16: {
+        PrecCopy &h = g->copies[QDD_PREC_F16S];
+        SapArgs<float, StF16, StF16, StF32, StF32> a{
+            g->geom, {h.links.as<__half2>(), nullptr}, {h.sclov.as<__half2>(), h.sclov_s.as<float>()},
+            {(float2 *)b.rho, nullptr}, {(float2 *)b.delta, nullptr}, {(float2 *)b.psi, nullptr},
             rs, ss, (float)g->kappa, colour, nmr, nrhs, first_psi, gather, gather_only, d_err};
         return dispatch_staging(g, a, s, pdl, timed);
     }

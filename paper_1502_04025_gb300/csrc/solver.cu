@@ -63,7 +63,7 @@ size_t workspace_bytes(const Gauge *g, int m, int B, qdd_prec sp, bool use_sap, 
     const qdd_prec zp = sp == QDD_PREC_F64 ? QDD_PREC_F64 : QDD_PREC_F32;
     size_t b = n * 16 * B * (size_t)(3 + m + 1) + n * ebytes(zp) * B * (size_t)m;
     if (use_sap) {
-        b += 2 * n * ebytes(sp) * B;
+        b += 2 * n * ebytes(spinor_store(sp)) * B;
         if (sp == QDD_PREC_F16S || sp == QDD_PREC_BF16S) b += 2 * V * 4 * B;
     }
     if (kdr > 0) b += n * 16 * B * (size_t)(3 * kdr + 1);
@@ -97,8 +97,8 @@ static qdd_status ensure_ws(Gauge *g, Workspace &w, int m, int B, qdd_prec sp, b
     QDD_TRY(w.V.ensure(c, n * 16 * B * (size_t)(m + 1)));
     QDD_TRY(w.Z.ensure(c, n * ebytes(zp) * B * (size_t)m));
     if (use_sap) {
-        QDD_TRY(w.rho.ensure(c, n * ebytes(sp) * B));
-        QDD_TRY(w.delta.ensure(c, n * ebytes(sp) * B));
+        QDD_TRY(w.rho.ensure(c, n * ebytes(spinor_store(sp)) * B));
+        QDD_TRY(w.delta.ensure(c, n * ebytes(spinor_store(sp)) * B));
         if (sp == QDD_PREC_F16S || sp == QDD_PREC_BF16S) {
             QDD_TRY(w.rho_s.ensure(c, V * 4 * B));
             QDD_TRY(w.delta_s.ensure(c, V * 4 * B));
@@ -133,7 +133,7 @@ qdd_status solve_impl(Gauge *g, Workspace *wsp, const double *b_in, double *x_ou
     Ctx *ctx = g->ctx;
     const int m = p->restart_m, B = p->nrhs;
     if (m < 1 || m > 64 || B < 1 || B > 64 || !(p->tol > 0) || p->max_restarts < 0 || p->nmr < 0 || p->ncy < 1 ||
-        p->sap_prec < QDD_PREC_F64 || p->sap_prec > QDD_PREC_BF16S ||
+        !is_sap_prec(p->sap_prec) ||
         (p->arnoldi_prec != QDD_PREC_F64 && p->arnoldi_prec != QDD_PREC_F32 && p->arnoldi_prec != QDD_PREC_DF64) ||
         p->reorth < 0 || p->reorth > 2 || p->dr_k < 0 || p->dr_k >= m) {
         set_error("invalid solve parameters");
@@ -201,7 +201,7 @@ qdd_status solve_impl(Gauge *g, Workspace *wsp, const double *b_in, double *x_ou
     bool pending_dr = false;     // the previous cycle ended ready for a deflated restart
     const int kdr = p->dr_k;
     w.hist.clear();
-    int iters = 0, restarts = 0;
+    int iters = 0, restarts = 0, deflated = 0;
     bool converged = false;
     qdd_status status = QDD_OK;
     SapBuffers sb{w.rho.p, w.delta.p, nullptr, w.rho_s.as<float>(), w.delta_s.as<float>()};
@@ -343,6 +343,7 @@ qdd_status solve_impl(Gauge *g, Workspace *wsp, const double *b_in, double *x_ou
             }
             j0 = kdr;
             restarts++;
+            deflated++;
         } else {
             for (int r = 0; r < B; r++)
                 QDD_TRY(blas_scale_by_norm(ctx, R0 + r * n, n, dev + sm.nrm1() + r, V + r * n, s));
@@ -364,7 +365,8 @@ qdd_status solve_impl(Gauge *g, Workspace *wsp, const double *b_in, double *x_ou
             char *zj = Z + (size_t)j * n * B * zb;
             // z_j = M v_j
             if (p->use_sap) {
-                QDD_TRY(launch_spinor_convert(g, vj, nullptr, QDD_PREC_F64, w.rho.p, w.rho_s.as<float>(), sp, B, s));
+                QDD_TRY(launch_spinor_convert(g, vj, nullptr, QDD_PREC_F64, w.rho.p, w.rho_s.as<float>(),
+                                              spinor_store(sp), B, s));
                 sb.psi = zj;
                 SeqScope seq(ctx->timer, K_SAP, s);
                 for (int hs = 0; hs < 2 * p->ncy; hs++)
@@ -535,6 +537,7 @@ qdd_status solve_impl(Gauge *g, Workspace *wsp, const double *b_in, double *x_ou
         long long l1 = 0;
         for (int c = 0; c < 4; c++) l1 += ctx->timer.launches[c];
         rep->kernel_launches = l1 - launches0;
+        rep->deflated_restarts = deflated;
         rep->n_history = (int)w.hist.size();
         rep->res_history = w.hist.data();
     }

@@ -19,9 +19,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libqdd.so")
 
 QDD_OK, QDD_EINVAL, QDD_ENOMEM, QDD_EBUDGET, QDD_ENOCONV, QDD_ENAN, QDD_ETIMEOUT, QDD_ECUDA, QDD_ENOTREADY = range(9)
-QDD_PREC_F64, QDD_PREC_F32, QDD_PREC_F16S, QDD_PREC_BF16S, QDD_PREC_DF64 = range(5)
+QDD_PREC_F64, QDD_PREC_F32, QDD_PREC_F16S, QDD_PREC_BF16S, QDD_PREC_DF64, QDD_PREC_H16 = range(6)
 PRECS = {"f64": QDD_PREC_F64, "f32": QDD_PREC_F32, "f16": QDD_PREC_F16S, "bf16": QDD_PREC_BF16S,
-         "df64": QDD_PREC_DF64}
+         "df64": QDD_PREC_DF64, "h16": QDD_PREC_H16}
 STATUS_NAMES = ["QDD_OK", "QDD_EINVAL", "QDD_ENOMEM", "QDD_EBUDGET", "QDD_ENOCONV", "QDD_ENAN", "QDD_ETIMEOUT",
                 "QDD_ECUDA", "QDD_ENOTREADY"]
 
@@ -41,6 +41,7 @@ class qdd_report(ctypes.Structure):
                 ("true_rel_res", ctypes.c_double), ("est_rel_res", ctypes.c_double), ("seconds", ctypes.c_double),
                 ("ms_sap", ctypes.c_double), ("ms_dslash", ctypes.c_double), ("ms_blas", ctypes.c_double),
                 ("sap_launches", ctypes.c_longlong), ("kernel_launches", ctypes.c_longlong),
+                ("deflated_restarts", ctypes.c_int),
                 ("n_history", ctypes.c_int), ("res_history", ctypes.POINTER(ctypes.c_double))]
 
     def as_dict(self) -> dict:

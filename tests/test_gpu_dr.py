@@ -40,19 +40,32 @@ def _rel_res(ora, S, x, b):
 
 
 def test_dr_matches_reference_and_beats_plain_restarts(q, ora, setup):
+    """Near (below) the critical kappa the few smallest eigenvalues slow plain
+    restarted FGMRES(16); keeping 6 harmonic Ritz vectors across restarts
+    saves steps (the reference: 217 against 240)."""
     S = setup
+    kappa = 0.138
+    A = ora.clover(L44, S["U"], 1.0, kappa)
+    Ainv = ora.invert_clover(L44, A)
+    g = q.qdd_create_gauge_field(S["ctx"], L44, DOM2, S["U"])
+    q.qdd_set_clover(g, 1.0, kappa)
     b = inputs.gaussian_source(L44, 2301)
-    P = S["dr"].Problem(L44, DOM2, S["U"], S["A"], S["Ainv"], S["kappa"], use_sap=False)
-    x_o, info = S["dr"].fgmres_dr(P, b.reshape(-1), 1e-11, m=10, k=5, max_cycles=200)
-    assert info["converged"]
-    common = dict(tol=1e-11, restart_m=10, use_sap=0, sap_prec="f64", arnoldi_prec="f64", max_restarts=300, reorth=2)
-    x_dr, r_dr = q.qdd_solve(S["g"], b, dr_k=5, **common)
-    x_pl, r_pl = q.qdd_solve(S["g"], b, dr_k=0, **common)
+    P = S["dr"].Problem(L44, DOM2, S["U"], A, Ainv, kappa, use_sap=False)
+    x_o, info = S["dr"].fgmres_dr(P, b.reshape(-1), 1e-11, m=16, k=6, max_cycles=200)
+    _, info_pl = S["dr"].fgmres_dr(P, b.reshape(-1), 1e-11, m=16, k=0, max_cycles=200)
+    assert info["converged"] and info["iters"] < info_pl["iters"]
+    common = dict(tol=1e-11, restart_m=16, use_sap=0, sap_prec="f64", arnoldi_prec="f64", max_restarts=300, reorth=2)
+    x_dr, r_dr = q.qdd_solve(g, b, dr_k=6, **common)
+    x_pl, r_pl = q.qdd_solve(g, b, dr_k=0, **common)
     assert r_dr["converged"] and r_pl["converged"]
-    assert _rel_res(ora, S, x_dr, b) <= 1e-11
-    assert abs(r_dr["iters"] - info["iters"]) <= max(3, info["iters"] // 10)
+    assert r_dr["deflated_restarts"] > 0 and r_pl["deflated_restarts"] == 0
+    r = b - ora.apply_D(L44, S["U"], A, kappa, x_dr)
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1e-11
+    assert abs(r_dr["iters"] - info["iters"]) <= max(3, info["iters"] // 20)
+    assert abs(r_pl["iters"] - info_pl["iters"]) <= max(3, info_pl["iters"] // 20)
     assert r_dr["iters"] < r_pl["iters"]
     assert np.linalg.norm(x_dr - x_o.reshape(b.shape)) <= 1e-8 * np.linalg.norm(x_o)
+    q.qdd_destroy_gauge(g)
 
 
 def test_dr_with_the_schwarz_preconditioner(q, ora, setup):
