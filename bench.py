@@ -73,7 +73,7 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--op-bench", action="store_true", help="time only the full-lattice operator")
     ap.add_argument("--op-lattice", default="32,32,32,64")
-    ap.add_argument("--op-precs", default="f32,f16,df64,f64")
+    ap.add_argument("--op-precs", default="f32,h16,f16,df64,f64")
     ap.add_argument("--op-iters", type=int, default=20)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
@@ -395,7 +395,7 @@ def run_qdd(args):
         ys = torch.empty_like(xs)
         Vl = int(np.prod(DSL["L"]))
         dslash = {"lattice": list(DSL["L"]), "flop_per_site": 1848}
-        for prec, bps in (("f32", 768), ("f16", 392), ("df64", 1536), ("f64", 1536)):
+        for prec, bps in (("f32", 768), ("h16", 484), ("f16", 392), ("df64", 1536), ("f64", 1536)):
             for _ in range(3):
                 qdd.qdd_apply_D(gd, xs, prec, out=ys)
             qdd.qdd_set_profiling(ctx, qdd.QDD_PROF_DSLASH)
@@ -472,7 +472,7 @@ def run_op_bench(args):
     out = {"metric": "Wilson-clover Dslash throughput", "unit": "GFLOP/s", "lattice": list(L),
            "domain": list(DSL["dom"]), "flop_per_site": 1848, "peak_hbm_gbs": pk["hbm_gbs"],
            "peak_kind": "of measured" if pk_kind == "measured" else "of fallback"}
-    bps_of = {"f32": 768, "f16": 392, "bf16": 392, "df64": 1536, "f64": 1536}
+    bps_of = {"f32": 768, "h16": 484, "f16": 392, "bf16": 392, "df64": 1536, "f64": 1536}
     for prec in args.op_precs.split(","):
         for _ in range(3):
             qdd.qdd_apply_D(g, xs, prec, out=ys)

@@ -183,12 +183,6 @@ qdd_status qdd_set_clover(qdd_gauge *g, double c_sw, double kappa);
  */
 qdd_status qdd_get_clover(qdd_gauge *g, int which, double *out);
 
-/* Schwarz kernel variant of this gauge field (a tuning choice; results agree
- * to rounding): 0 automatic (= 1), 1 one thread per even/odd site pair, 2 two
- * threads per pair (FP32-arithmetic precisions and domains of a multiple of
- * 32 sites; otherwise 1 is used). */
-qdd_status qdd_set_sap_variant(qdd_gauge *g, int variant);
-
 /* ------------------------------------------------------------- operators */
 
 /*
@@ -289,7 +283,6 @@ qdd_status qdd_layout(const int L[4], const int dom[4], int *site_of, uint16_t *
 
 typedef struct {
     int dom[4];        /* fastest domain shape */
-    int sap_variant;   /* its Schwarz kernel variant (qdd_set_sap_variant) */
     int nmr;           /* its MR step count */
     int iters;         /* Arnoldi steps it needed */
     int n_tried;       /* candidates timed */

@@ -327,6 +327,9 @@ qdd_status qdd_create_gauge_field(qdd_ctx *ctx, const int L[4], const int dom[4]
     QDD_TRY(g->d_nbd.alloc(ctx, hg.nbd.size() * sizeof(int)));
     QDD_TRY(g->d_site_of.alloc(ctx, hg.site_of.size() * sizeof(int)));
     QDD_TRY(g->d_block_slot.alloc(ctx, hg.block_slot.size() * sizeof(int)));
+    QDD_TRY(g->d_fcoord.alloc(ctx, hg.fcoord.size() * sizeof(uint32_t)));
+    QDD_CUDA(cudaMemcpy(g->d_fcoord.p, hg.fcoord.data(), hg.fcoord.size() * sizeof(uint32_t),
+                        cudaMemcpyHostToDevice));
     QDD_CUDA(cudaMemcpy(g->d_block_slot.p, hg.block_slot.data(), hg.block_slot.size() * sizeof(int),
                         cudaMemcpyHostToDevice));
     QDD_CUDA(cudaMemcpy(g->d_nbl.p, hg.nbl.data(), hg.nbl.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
@@ -350,6 +353,9 @@ qdd_status qdd_create_gauge_field(qdd_ctx *ctx, const int L[4], const int dom[4]
     G.nbl = g->d_nbl.as<uint16_t>();
     G.nbd = g->d_nbd.as<int>();
     G.block_slot = g->d_block_slot.as<int>();
+    G.fcoord = g->d_fcoord.as<uint32_t>();
+    for (int k = 0; k < 8; k++) G.foff[k] = hg.foff[k];
+    G.nf = hg.nf;
 
     const size_t lbytes = (size_t)hg.V * 36 * sizeof(double2);
     QDD_TRY(g->links64.alloc(ctx, lbytes));
@@ -447,17 +453,6 @@ qdd_status qdd_get_clover(qdd_gauge *g, int which, double *out)
     return QDD_OK;
 }
 
-qdd_status qdd_set_sap_variant(qdd_gauge *g, int variant)
-{
-    clear_error();
-    if (!g || variant < 0 || variant > 2) {
-        set_error("invalid argument");
-        return QDD_EINVAL;
-    }
-    g->sap_variant = variant;
-    return QDD_OK;
-}
-
 qdd_status qdd_apply_D(qdd_gauge *g, const double *in, double *out, int nrhs, qdd_prec prec, int on_device,
                        void *stream)
 {
@@ -511,24 +506,21 @@ qdd_status qdd_sap_apply(qdd_gauge *g, const double *eta, double *psi, double *r
     auto &st = stg[g];
     if (!st) st.reset(new Staging());
     const size_t V = g->hg.V;
-    const qdd_prec ssp = spinor_store(prec);                                 // rho, delta storage
+    const qdd_prec ssp = spinor_store(prec);                                 // rho storage
     const size_t eb = elem_bytes(ssp);
     const qdd_prec pp = prec == QDD_PREC_F64 ? QDD_PREC_F64 : QDD_PREC_F32;  // psi storage
     const bool scaled = prec == QDD_PREC_F16S || prec == QDD_PREC_BF16S;
     const double *din = nullptr;
     QDD_TRY(stage_in(g, st->io, eta, nrhs, on_device, s, &din));
     QDD_TRY(st->a.ensure(g->ctx, V * 12 * eb * nrhs));                  // rho
-    QDD_TRY(st->b.ensure(g->ctx, V * 12 * eb * nrhs));                  // delta
+    QDD_TRY(st->b.ensure(g->ctx, sap_face_bytes(g->hg, prec, nrhs)));   // face slots
     QDD_TRY(st->c.ensure(g->ctx, V * 12 * elem_bytes(pp) * nrhs));      // psi
     QDD_TRY(st->err.ensure(g->ctx, sizeof(int)));
-    if (scaled) {
-        QDD_TRY(st->a_s.ensure(g->ctx, V * 4 * nrhs));
-        QDD_TRY(st->b_s.ensure(g->ctx, V * 4 * nrhs));
-    }
+    if (scaled) QDD_TRY(st->a_s.ensure(g->ctx, V * 4 * nrhs));
     QDD_CUDA(cudaMemsetAsync(st->err.p, 0, sizeof(int), s));
     QDD_TRY(launch_spinor_in(g, din, st->a.p, st->a_s.as<float>(), ssp, nrhs, s));
     if (n_half < 2) QDD_CUDA(cudaMemsetAsync(st->c.p, 0, V * 12 * elem_bytes(pp) * nrhs, s));
-    SapBuffers b{st->a.p, st->b.p, st->c.p, st->a_s.as<float>(), st->b_s.as<float>()};
+    SapBuffers b{st->a.p, st->b.p, st->c.p, st->a_s.as<float>()};
     {
         SeqScope seq(g->ctx->timer, K_SAP, s);
         for (int hs = 0; hs < n_half; hs++)

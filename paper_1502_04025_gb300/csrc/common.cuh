@@ -163,6 +163,12 @@ struct Geom {
     const uint16_t *nbl;   // [Vd][8]: neighbour site slot (wrapped into the domain), bit 15 = leaves the domain
     const int *nbd;        // [Nd][8]: neighbour domain slot
     const int *block_slot; // [Nd]: slot of the domain with lexicographic block index b
+    // Face slots of a domain (one per hop that leaves it): direction dir's
+    // slots start at foff[dir] and are indexed by the site's coordinates
+    // transverse to mu = dir/2, which a hop and its reverse share.
+    const uint32_t *fcoord;  // [Vd]: byte mu = transverse index of the site for direction mu
+    int foff[8];
+    int nf;                  // face slots per domain
 };
 
 // Site of thread index gi when the lattice is walked domain by domain in

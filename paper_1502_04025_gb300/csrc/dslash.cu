@@ -150,20 +150,57 @@ __device__ __forceinline__ cdf ld_in_df(const double2 *p)
     return {df_from_double(v.x), df_from_double(v.y)};
 }
 
-template <int MU, int SGN>
-__device__ __forceinline__ void hop_df(const cdf *U, const cdf *x, cdfacc *acc)
+// Spin structure of one hop in the chiral basis.  With u the upper and l the
+// lower two spins, (1 -+ gamma_mu) x projects to h = u -+ A l and the lower
+// spins of the result are -+ A^dagger (U h), where A is a 2x2 matrix of unit
+// complex numbers, anti-diagonal for x, y and diagonal for z, t:
+//   x: A = [[0, -i], [-i, 0]]   y: A = [[0, -1], [1, 0]]
+//   z: A = [[-i, 0], [0, i]]    t: A = 1
+// One direction and sign is therefore a swap flag, a rotate-by-i flag and
+// four signs.  The double-float operator runs one hop body driven by these
+// runtime values: eight inlined copies of its long double-float chains did
+// not fit the instruction cache.
+struct HopSpin {
+    bool swap, rot;
+    float p0, p1;  // h_0 = u_0 + p0 (rot ? i : 1) l_{swap}, h_1 = u_1 + p1 (rot ? i : 1) l_{1-swap}
+    float r0, r1;  // lower_0 += r0 (rot ? i : 1) w_{swap}, lower_1 += r1 (rot ? i : 1) w_{1-swap}
+};
+
+__device__ __forceinline__ HopSpin hop_spin(int mu, int back)
+{
+    const bool swap = mu < 2, rot = (mu & 1) == 0;
+    const float s0 = mu == 3 ? 1.f : -1.f;  // A's row-0 entry = s0 (rot ? i : 1)
+    const float s1 = mu == 0 ? -1.f : 1.f;  // A's row-1 entry = s1 (rot ? i : 1)
+    const float t = back ? 1.f : -1.f;      // forward hop: h = u - A l; backward: h = u + A l
+    // rows of A^dagger: conjugate transpose; conjugation flips an imaginary unit
+    float d0 = swap ? s1 : s0, d1 = swap ? s0 : s1;
+    if (rot) {
+        d0 = -d0;
+        d1 = -d1;
+    }
+    return {swap, rot, t * s0, t * s1, t * d0, t * d1};
+}
+
+// sg * (rot ? i z : z), exact
+__device__ __forceinline__ cdf cdf_unit(bool rot, float sg, cdf z)
+{
+    df a = rot ? df_neg(z.im) : z.re;
+    df b = rot ? z.re : z.im;
+    return {{__fmul_rn(sg, a.hi), __fmul_rn(sg, a.lo)}, {__fmul_rn(sg, b.hi), __fmul_rn(sg, b.lo)}};
+}
+
+__device__ __forceinline__ cdf cdf_sel(bool c, cdf a, cdf b) { return c ? a : b; }
+
+// acc += hop contribution; U is the oriented link (U(n) for a forward hop,
+// U(n - mu)^dagger for a backward one), row-major
+__device__ __forceinline__ void hop_df_rt(const HopSpin &hs, const cdf *U, const cdf *x, cdfacc *acc)
 {
     cdf h[6];
 #pragma unroll
     for (int c = 0; c < 3; c++) {
-        cdf u0 = x[0 * 3 + c], u1 = x[1 * 3 + c], l0 = x[2 * 3 + c], l1 = x[3 * 3 + c];
-        cdf al0, al1;
-        if (MU == 0) { al0 = cdf_tmi(l1); al1 = cdf_tmi(l0); }
-        else if (MU == 1) { al0 = cdf_neg(l1); al1 = l0; }
-        else if (MU == 2) { al0 = cdf_tmi(l0); al1 = cdf_ti(l1); }
-        else { al0 = l0; al1 = l1; }
-        if (SGN > 0) { h[c] = cdf_sub(u0, al0); h[3 + c] = cdf_sub(u1, al1); }
-        else { h[c] = cdf_add(u0, al0); h[3 + c] = cdf_add(u1, al1); }
+        cdf l0 = x[6 + c], l1 = x[9 + c];
+        h[c] = cdf_add(x[c], cdf_unit(hs.rot, hs.p0, cdf_sel(hs.swap, l1, l0)));
+        h[3 + c] = cdf_add(x[3 + c], cdf_unit(hs.rot, hs.p1, cdf_sel(hs.swap, l0, l1)));
     }
     cdf w[6];
 #pragma unroll
@@ -173,47 +210,18 @@ __device__ __forceinline__ void hop_df(const cdf *U, const cdf *x, cdfacc *acc)
             cdfacc t;
             cdfacc_zero(t);
 #pragma unroll
-            for (int b = 0; b < 3; b++) {
-                if (SGN < 0) cdfacc_mul_add<true>(t, U[b * 3 + a], h[sp * 3 + b]);
-                else cdfacc_mul_add<false>(t, U[a * 3 + b], h[sp * 3 + b]);
-            }
+            for (int b = 0; b < 3; b++) cdfacc_mul_add<false>(t, U[a * 3 + b], h[sp * 3 + b]);
             w[sp * 3 + a] = cdfacc_value(t);
         }
 #pragma unroll
     for (int c = 0; c < 3; c++) {
         cdf w0 = w[c], w1 = w[3 + c];
-        cdf b0, b1;
-        if (MU == 0) { b0 = cdf_ti(w1); b1 = cdf_ti(w0); }
-        else if (MU == 1) { b0 = w1; b1 = cdf_neg(w0); }
-        else if (MU == 2) { b0 = cdf_ti(w0); b1 = cdf_tmi(w1); }
-        else { b0 = w0; b1 = w1; }
-        if (SGN > 0) { b0 = cdf_neg(b0); b1 = cdf_neg(b1); }
+        cdf b0 = cdf_unit(hs.rot, hs.r0, cdf_sel(hs.swap, w1, w0));
+        cdf b1 = cdf_unit(hs.rot, hs.r1, cdf_sel(hs.swap, w0, w1));
         dfacc_add(acc[0 * 3 + c].re, w0.re); dfacc_add(acc[0 * 3 + c].im, w0.im);
         dfacc_add(acc[1 * 3 + c].re, w1.re); dfacc_add(acc[1 * 3 + c].im, w1.im);
         dfacc_add(acc[2 * 3 + c].re, b0.re); dfacc_add(acc[2 * 3 + c].im, b0.im);
         dfacc_add(acc[3 * 3 + c].re, b1.re); dfacc_add(acc[3 * 3 + c].im, b1.im);
-    }
-}
-
-template <int MU, typename SI>
-__device__ __forceinline__ void dslash_dir_df(const Geom &g, const float4 *U, const typename SI::T2 *in,
-                                              int64_t rbase, int d, int s, cdfacc *acc)
-{
-    cdf u[9], x[12];
-#pragma unroll
-    for (int b = 0; b < 2; b++) {
-        uint16_t e = __ldg(g.nbl + s * 8 + 2 * MU + b);
-        int nd = (e & kCross) ? __ldg(g.nbd + d * 8 + 2 * MU + b) : d;
-        int ns = e & kSlotMask;
-        const typename SI::T2 *xp = in + rbase + (int64_t)nd * 12 * g.Vd + ns;
-#pragma unroll
-        for (int k = 0; k < 12; k++) x[k] = ld_in_df(xp + (int64_t)k * g.Vd);
-        int ld = b ? nd : d, ls = b ? ns : s;
-        const float4 *up = U + ((int64_t)ld * 36 + MU * 9) * g.Vd + ls;
-#pragma unroll
-        for (int k = 0; k < 9; k++) u[k] = ld_cdf(up + (int64_t)k * g.Vd);
-        if (b == 0) hop_df<MU, +1>(u, x, acc);
-        else hop_df<MU, -1>(u, x, acc);
     }
 }
 
@@ -229,15 +237,37 @@ __global__ void __launch_bounds__(128) k_dslash_df(Geom g, const float4 *U, cons
     cdfacc acc[12];
 #pragma unroll
     for (int k = 0; k < 12; k++) cdfacc_zero(acc[k]);
-    dslash_dir_df<0, SI>(g, U, in, rbase, d, s, acc);
-    dslash_dir_df<1, SI>(g, U, in, rbase, d, s, acc);
-    dslash_dir_df<2, SI>(g, U, in, rbase, d, s, acc);
-    dslash_dir_df<3, SI>(g, U, in, rbase, d, s, acc);
+#pragma unroll 1
+    for (int dir = 0; dir < 8; dir++) {
+        const int mu = dir >> 1, back = dir & 1;
+        uint16_t e = __ldg(g.nbl + s * 8 + dir);
+        int nd = (e & kCross) ? __ldg(g.nbd + d * 8 + dir) : d;
+        int ns = e & kSlotMask;
+        cdf x[12], u[9];
+        const typename SI::T2 *xp = in + rbase + (int64_t)nd * 12 * g.Vd + ns;
+#pragma unroll
+        for (int k = 0; k < 12; k++) x[k] = ld_in_df(xp + (int64_t)k * g.Vd);
+        const int ld = back ? nd : d, ls = back ? ns : s;
+        const float4 *up = U + ((int64_t)ld * 36 + mu * 9) * g.Vd + ls;
+#pragma unroll
+        for (int k = 0; k < 9; k++) {
+            // backward hop: element (a, b) of U^dagger is conj(U_ba)
+            const int src = back ? (k % 3) * 3 + k / 3 : k;
+            cdf v = ld_cdf(up + (int64_t)src * g.Vd);
+            u[k] = back ? cdf{v.re, df_neg(v.im)} : v;
+        }
+        hop_df_rt(hop_spin(mu, back), u, x, acc);
+    }
+    // y = A x - kappa * (hop sum), one chirality block per iteration; the
+    // block's hop sum is always hv[0..5] (the second block is shifted down)
+    cdf hv[12];
+#pragma unroll
+    for (int k = 0; k < 12; k++) hv[k] = cdfacc_value(acc[k]);
     const typename SI::T2 *xp = in + rbase + (int64_t)d * 12 * g.Vd + s;
     const float4 *ap = A + (int64_t)d * 36 * g.Vd + s;
     double2 *op = out + rbase + (int64_t)d * 12 * g.Vd + s;
     const df mk_ = df_neg(kappa);
-#pragma unroll
+#pragma unroll 1
     for (int blk = 0; blk < 2; blk++) {
         cdf x[6], m[18];
 #pragma unroll
@@ -263,11 +293,11 @@ __global__ void __launch_bounds__(128) k_dslash_df(Geom g, const float4 *U, cons
             }
 #pragma unroll
         for (int i = 0; i < 6; i++) {
-            cdf hv = cdfacc_value(acc[6 * blk + i]);
-            dfacc_mul_add(y[i].re, mk_, hv.re);
-            dfacc_mul_add(y[i].im, mk_, hv.im);
+            dfacc_mul_add(y[i].re, mk_, hv[i].re);
+            dfacc_mul_add(y[i].im, mk_, hv[i].im);
             cdf v = cdfacc_value(y[i]);
             op[(int64_t)(6 * blk + i) * g.Vd] = make_double2(df_to_double(v.re), df_to_double(v.im));
+            hv[i] = hv[6 + i];
         }
     }
 }

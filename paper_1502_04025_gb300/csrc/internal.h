@@ -150,6 +150,9 @@ struct HostGeom {
     std::vector<int> site_of;      // internal index -> host site index
     std::vector<uint16_t> nbl;     // [Vd][8]
     std::vector<int> nbd;          // [Nd][8]
+    std::vector<uint32_t> fcoord;  // [Vd]: byte mu = index of the site's coordinates transverse to mu
+    int foff[8] = {0};             // first face slot of each direction
+    int nf = 0;                    // face slots per domain
 };
 
 qdd_status make_geometry(const int L[4], const int dom[4], HostGeom &hg);
@@ -165,7 +168,7 @@ struct PrecCopy {
 struct Workspace {
     int nrhs = 0, m = 0;
     qdd_prec sp = QDD_PREC_F32;
-    DevMem io, b, x, V, Z, rho, rho_s, delta, delta_s, dev, scratch, err;
+    DevMem io, b, x, V, Z, rho, rho_s, face, dev, scratch, err;
     DevMem ZR, Vt, ZRt, P;  // deflated restarts: recycled z (FP64), temporaries, P matrices
     double2 *host = nullptr;  // pinned mirror of `dev`
     size_t host_elems = 0;
@@ -180,7 +183,7 @@ struct Gauge {
     Ctx *ctx = nullptr;
     HostGeom hg;
     Geom geom{};
-    DevMem d_nbl, d_nbd, d_site_of, d_block_slot;
+    DevMem d_nbl, d_nbd, d_site_of, d_block_slot, d_fcoord;
     DevMem links64;           // FP64 links, internal layout
     bool have_clover = false;
     double csw = 0, kappa = 0;
@@ -189,7 +192,6 @@ struct Gauge {
     std::unique_ptr<Workspace> ws;  // workspace of the synchronous entry points
     std::mutex mu;            // one synchronous call at a time per gauge object
     std::mutex copy_mu;       // guards the lazily built precision copies
-    int sap_variant = 0;      // Schwarz kernel: 0 automatic, 1 one thread per site pair, 2 two
     ~Gauge();
 };
 
@@ -239,8 +241,8 @@ qdd_status launch_dslash(Gauge *g, qdd_prec arith, qdd_prec fields_prec, const v
 
 // sap.cu: one half-sweep over the domains of `colour`
 struct SapBuffers {
-    void *rho, *delta, *psi;
-    float *rho_s, *delta_s;
+    void *rho, *face, *psi;  // face: sap_face_bytes() of face slots
+    float *rho_s;
 };
 // gather_only: apply the pending inter-domain update to the residual of the
 // domains of `colour` and store it, without a block solve.
@@ -248,6 +250,8 @@ struct SapBuffers {
 // CTAs may start early and stage read-only data; it must directly follow a
 // half-sweep in the stream).  timed: bracket this launch with profiling
 // events (false when the caller times a whole preconditioner application).
+// Bytes of the face slots of all domains (the inter-domain update in flight).
+size_t sap_face_bytes(const HostGeom &hg, qdd_prec prec, int nrhs);
 qdd_status launch_sap_halfsweep(Gauge *g, qdd_prec prec, const SapBuffers &b, int colour, int nmr, int nrhs,
                                 int first_psi, int gather, int gather_only, int *d_err, cudaStream_t s,
                                 bool pdl = false, bool timed = true);

@@ -115,6 +115,30 @@ qdd_status make_geometry(const int L[4], const int dom[4], HostGeom &hg)
                 hg.nbl[(size_t)s * 8 + 2 * mu + b] = (uint16_t)(local_slot(hg.dom, hg.Vh, cc) | cross);
             }
     }
+    // face slots: the hops that leave a domain, direction by direction; within
+    // direction mu (either sign) a site's slot is the lexicographic index of
+    // its coordinates transverse to mu, shared by the site across the face
+    hg.nf = 0;
+    for (int dir = 0; dir < 8; dir++) {
+        hg.foff[dir] = hg.nf;
+        hg.nf += hg.Vd / hg.dom[dir >> 1];
+    }
+    hg.fcoord.assign(hg.Vd, 0);
+    for (int s = 0; s < hg.Vd; s++) {
+        int c[4];
+        local_coords(hg.dom, hg.Vh, s, c);
+        uint32_t packed = 0;
+        for (int mu = 0; mu < 4; mu++) {
+            int t = 0, stride = 1;
+            for (int nu = 0; nu < 4; nu++)
+                if (nu != mu) {
+                    t += c[nu] * stride;
+                    stride *= hg.dom[nu];
+                }
+            packed |= (uint32_t)t << (8 * mu);  // t < Vd / dom[mu] <= 256
+        }
+        hg.fcoord[s] = packed;
+    }
     // domain neighbour table
     hg.nbd.assign((size_t)hg.Nd * 8, 0);
     for (int d = 0; d < hg.Nd; d++) {

@@ -63,8 +63,8 @@ size_t workspace_bytes(const Gauge *g, int m, int B, qdd_prec sp, bool use_sap, 
     const qdd_prec zp = sp == QDD_PREC_F64 ? QDD_PREC_F64 : QDD_PREC_F32;
     size_t b = n * 16 * B * (size_t)(3 + m + 1) + n * ebytes(zp) * B * (size_t)m;
     if (use_sap) {
-        b += 2 * n * ebytes(spinor_store(sp)) * B;
-        if (sp == QDD_PREC_F16S || sp == QDD_PREC_BF16S) b += 2 * V * 4 * B;
+        b += n * ebytes(spinor_store(sp)) * B + sap_face_bytes(g->hg, sp, B);
+        if (sp == QDD_PREC_F16S || sp == QDD_PREC_BF16S) b += V * 4 * B;
     }
     if (kdr > 0) b += n * 16 * B * (size_t)(3 * kdr + 1);
     return b + (1 << 20);
@@ -72,7 +72,7 @@ size_t workspace_bytes(const Gauge *g, int m, int B, qdd_prec sp, bool use_sap, 
 
 size_t workspace_held(const Workspace *w)
 {
-    const DevMem *all[] = {&w->io, &w->b, &w->x, &w->V, &w->Z, &w->rho, &w->rho_s, &w->delta, &w->delta_s,
+    const DevMem *all[] = {&w->io, &w->b, &w->x, &w->V, &w->Z, &w->rho, &w->rho_s, &w->face,
                            &w->dev, &w->scratch, &w->err, &w->ZR, &w->Vt, &w->ZRt, &w->P};
     size_t t = 0;
     for (auto *d : all) t += d->bytes;
@@ -81,7 +81,7 @@ size_t workspace_held(const Workspace *w)
 
 void workspace_release(Workspace *w)
 {
-    DevMem *all[] = {&w->io, &w->b, &w->x, &w->V, &w->Z, &w->rho, &w->rho_s, &w->delta, &w->delta_s,
+    DevMem *all[] = {&w->io, &w->b, &w->x, &w->V, &w->Z, &w->rho, &w->rho_s, &w->face,
                      &w->dev, &w->scratch, &w->err, &w->ZR, &w->Vt, &w->ZRt, &w->P};
     for (auto *d : all) d->release();
 }
@@ -98,11 +98,8 @@ static qdd_status ensure_ws(Gauge *g, Workspace &w, int m, int B, qdd_prec sp, b
     QDD_TRY(w.Z.ensure(c, n * ebytes(zp) * B * (size_t)m));
     if (use_sap) {
         QDD_TRY(w.rho.ensure(c, n * ebytes(spinor_store(sp)) * B));
-        QDD_TRY(w.delta.ensure(c, n * ebytes(spinor_store(sp)) * B));
-        if (sp == QDD_PREC_F16S || sp == QDD_PREC_BF16S) {
-            QDD_TRY(w.rho_s.ensure(c, V * 4 * B));
-            QDD_TRY(w.delta_s.ensure(c, V * 4 * B));
-        }
+        QDD_TRY(w.face.ensure(c, sap_face_bytes(g->hg, sp, B)));
+        if (sp == QDD_PREC_F16S || sp == QDD_PREC_BF16S) QDD_TRY(w.rho_s.ensure(c, V * 4 * B));
     }
     if (kdr > 0) {
         QDD_TRY(w.ZR.ensure(c, n * 16 * B * (size_t)kdr));
@@ -204,7 +201,7 @@ qdd_status solve_impl(Gauge *g, Workspace *wsp, const double *b_in, double *x_ou
     int iters = 0, restarts = 0, deflated = 0;
     bool converged = false;
     qdd_status status = QDD_OK;
-    SapBuffers sb{w.rho.p, w.delta.p, nullptr, w.rho_s.as<float>(), w.delta_s.as<float>()};
+    SapBuffers sb{w.rho.p, w.face.p, nullptr, w.rho_s.as<float>()};
     double2 *ZR = w.ZR.as<double2>();
 
     for (int cycle = 0;; cycle++) {

@@ -1,5 +1,5 @@
-// Autotuner: domain shape, Schwarz kernel variant and MR step count for a
-// given lattice, precision and number of right-hand sides.
+// Autotuner: domain shape and MR step count for a given lattice, precision
+// and number of right-hand sides.
 //
 // The paper picks 4^4 or 8x4^3 domains so that a domain fits a core's cache
 // (Sec. 3.3), finds 4-5 MR steps optimal for time-to-solution (Sec. 3.7) and
@@ -84,44 +84,39 @@ extern "C" qdd_status qdd_autotune(qdd_ctx *ctx, const int L[4], const double *l
             return s;
         }
         const double load = qdd_load_model(g->hg.Nd2, (double)ctx->nsm);
-        for (int variant = 1; variant <= 2; variant++) {
-            if (variant == 2 && (p->sap_prec == QDD_PREC_F64 || g->hg.Vd % 32)) continue;
-            g->sap_variant = variant;
-            const int nn = n_nmr > 0 ? n_nmr : 1;
-            for (int k = 0; k < nn; k++) {
-                qdd_solve_params q = *p;
-                if (n_nmr > 0) q.nmr = nmr_candidates[k];
-                qdd_report rep;
-                // one untimed solve (buffers, copies), then one timed
-                s = solve_impl(g, g->ws ? g->ws.get() : (g->ws = make_workspace()).get(), bd, xdev.as<double>(), 1,
-                               &q, &rep, st);
-                if (s != QDD_OK && s != QDD_ENOCONV) {
-                    qdd_destroy_gauge(g);
-                    cudaStreamDestroy(st);
-                    return s;
-                }
-                QDD_CUDA(cudaEventRecord(e0, st));
-                s = solve_impl(g, g->ws.get(), bd, xdev.as<double>(), 1, &q, &rep, st);
-                QDD_CUDA(cudaEventRecord(e1, st));
-                QDD_CUDA(cudaEventSynchronize(e1));
-                float ms = 0;
-                QDD_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-                tried++;
-                bool ok = (s == QDD_OK) && rep.converged;
-                appendf(js,
-                        "%s{\"dom\":[%d,%d,%d,%d],\"variant\":%d,\"nmr\":%d,\"ms\":%.4f,\"iters\":%d,"
-                        "\"restarts\":%d,\"converged\":%s,\"domains_per_colour\":%d,\"wave_load\":%.4f}",
-                        first ? "" : ",", dom[0], dom[1], dom[2], dom[3], variant, q.nmr, ms, rep.iters, rep.restarts,
-                        ok ? "true" : "false", g->hg.Nd2, load);
-                first = false;
-                if (ok && (out->ms < 0 || ms < out->ms)) {
-                    out->ms = ms;
-                    std::memcpy(out->dom, dom, 4 * sizeof(int));
-                    out->sap_variant = variant;
-                    out->nmr = q.nmr;
-                    out->iters = rep.iters;
-                    out->wave_load = load;
-                }
+        const int nn = n_nmr > 0 ? n_nmr : 1;
+        for (int k = 0; k < nn; k++) {
+            qdd_solve_params q = *p;
+            if (n_nmr > 0) q.nmr = nmr_candidates[k];
+            qdd_report rep;
+            // one untimed solve (buffers, copies), then one timed
+            s = solve_impl(g, g->ws ? g->ws.get() : (g->ws = make_workspace()).get(), bd, xdev.as<double>(), 1, &q,
+                           &rep, st);
+            if (s != QDD_OK && s != QDD_ENOCONV) {
+                qdd_destroy_gauge(g);
+                cudaStreamDestroy(st);
+                return s;
+            }
+            QDD_CUDA(cudaEventRecord(e0, st));
+            s = solve_impl(g, g->ws.get(), bd, xdev.as<double>(), 1, &q, &rep, st);
+            QDD_CUDA(cudaEventRecord(e1, st));
+            QDD_CUDA(cudaEventSynchronize(e1));
+            float ms = 0;
+            QDD_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            tried++;
+            bool ok = (s == QDD_OK) && rep.converged;
+            appendf(js,
+                    "%s{\"dom\":[%d,%d,%d,%d],\"nmr\":%d,\"ms\":%.4f,\"iters\":%d,\"restarts\":%d,"
+                    "\"converged\":%s,\"domains_per_colour\":%d,\"wave_load\":%.4f}",
+                    first ? "" : ",", dom[0], dom[1], dom[2], dom[3], q.nmr, ms, rep.iters, rep.restarts,
+                    ok ? "true" : "false", g->hg.Nd2, load);
+            first = false;
+            if (ok && (out->ms < 0 || ms < out->ms)) {
+                out->ms = ms;
+                std::memcpy(out->dom, dom, 4 * sizeof(int));
+                out->nmr = q.nmr;
+                out->iters = rep.iters;
+                out->wave_load = load;
             }
         }
         qdd_destroy_gauge(g);

@@ -51,7 +51,7 @@ class qdd_report(ctypes.Structure):
 
 
 class qdd_tune_result(ctypes.Structure):
-    _fields_ = [("dom", ctypes.c_int * 4), ("sap_variant", ctypes.c_int), ("nmr", ctypes.c_int),
+    _fields_ = [("dom", ctypes.c_int * 4), ("nmr", ctypes.c_int),
                 ("iters", ctypes.c_int), ("n_tried", ctypes.c_int), ("ms", ctypes.c_double),
                 ("wave_load", ctypes.c_double)]
 
@@ -72,7 +72,6 @@ _SIGS = {
     "qdd_destroy_gauge": (None, [_vp]),
     "qdd_set_clover": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double]),
     "qdd_get_clover": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
-    "qdd_set_sap_variant": (ctypes.c_int, [_vp, ctypes.c_int]),
     "qdd_apply_D": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp]),
     "qdd_sap_apply": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_int, _vp]),
@@ -215,10 +214,6 @@ def qdd_get_clover(g, V: int, which: int = 0) -> np.ndarray:
     return out
 
 
-def qdd_set_sap_variant(g, variant: int):
-    _check(_lib.qdd_set_sap_variant(g, int(variant)), "qdd_set_sap_variant")
-
-
 # --------------------------------------------------------------- operators
 
 def qdd_apply_D(g, x, prec="f64", nrhs: int = 1, out=None):
@@ -313,7 +308,7 @@ def qdd_layout(L, dom):
 
 def qdd_autotune(ctx, L, links, c_sw: float, kappa: float, b, params: qdd_solve_params, dom_candidates,
                  nmr_candidates=()):
-    """Fastest (dom, kernel variant, nmr) for this problem; returns (result dict, per-candidate log)."""
+    """Fastest (dom, nmr) for this problem; returns (result dict, per-candidate log)."""
     import json
 
     pl, ldev = _ptr(links)
@@ -325,7 +320,7 @@ def qdd_autotune(ctx, L, links, c_sw: float, kappa: float, b, params: qdd_solve_
     _check(_lib.qdd_autotune(ctx, _ivec(L), pl, ldev, float(c_sw), float(kappa), pb, bdev, ctypes.byref(params),
                              doms, len(dom_candidates), nmrs, len(nmr_candidates), ctypes.byref(res), buf,
                              len(buf)), "qdd_autotune")
-    out = {"dom": tuple(res.dom), "sap_variant": res.sap_variant, "nmr": res.nmr, "iters": res.iters,
+    out = {"dom": tuple(res.dom), "nmr": res.nmr, "iters": res.iters,
            "n_tried": res.n_tried, "ms": res.ms, "wave_load": res.wave_load}
     return out, json.loads(buf.value.decode())
 

@@ -115,7 +115,7 @@ def test_autotune_picks_a_converged_shape(q, ora):
     cands = [(4, 4, 4, 4), (8, 4, 4, 4), (4, 2, 2, 2), (16, 4, 4, 4)]  # the last leaves one block in x
     res, log = q.qdd_autotune(ctx, L, U, 1.0, 0.125, b, p, cands, nmr_candidates=(2, 4))
     timed = [c for c in log if "ms" in c]
-    assert res["n_tried"] == len(timed) and len(timed) >= 6
+    assert res["n_tried"] == len(timed) and len(timed) >= 4
     assert any("error" in c for c in log)
     best = min((c for c in timed if c["converged"]), key=lambda c: c["ms"])
     assert tuple(best["dom"]) == res["dom"] and best["nmr"] == res["nmr"]
@@ -124,7 +124,6 @@ def test_autotune_picks_a_converged_shape(q, ora):
     # the chosen setting solves the problem
     g = q.qdd_create_gauge_field(ctx, L, res["dom"], U)
     q.qdd_set_clover(g, 1.0, 0.125)
-    q.qdd_set_sap_variant(g, res["sap_variant"])
     x, rep = q.qdd_solve(g, b, q.qdd_default_params(tol=1e-10, sap_prec="f32", nmr=res["nmr"]))
     A = ora.clover(L, U, 1.0, 0.125)
     r = b - ora.apply_D(L, U, A, 0.125, x)
