@@ -149,15 +149,20 @@ static void worker_main(Ctx *ctx)
                 std::vector<double>().swap(r->b);  // the source copy is no longer needed
                 r0 += r->p.nrhs;
             }
-            ctx->running--;
         }
+        ctx->done_cv.notify_all();  // results are out; this worker still counts as running
         // a large idle workspace would block the admission of other requests:
-        // give it back (small ones are kept for reuse)
+        // give it back (small ones are kept for reuse) before this worker stops
+        // counting as running, so that admission never sees an idle device
+        // whose memory is still held and rejects a request that would fit
         if (workspace_held(ws.get()) > ((size_t)4 << 30)) workspace_release(ws.get());
         // keep the merge buffers only while they are small
         if (bm.size() > ((size_t)1 << 27)) std::vector<double>().swap(bm);
         if (xm.size() > ((size_t)1 << 27)) std::vector<double>().swap(xm);
-        ctx->done_cv.notify_all();
+        {
+            std::lock_guard<std::mutex> lk(ctx->q_mu);
+            ctx->running--;
+        }
         ctx->q_cv.notify_all();
     }
 }
