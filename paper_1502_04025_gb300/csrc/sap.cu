@@ -487,24 +487,44 @@ __global__ void __launch_bounds__(256) k_sap(const SapArgs<R, SL, SC, SS, SP> a)
         }
         // rho_e parks in sR until the setup phase, rho_o in sRo (once every
         // thread has read the staged face slots that overlap it)
+        // (the two sites run through one copy of the face code: a loop with
+        // element-wise selects, which keeps the kernel in the instruction cache)
         cpx<R> acc[12];
         if (rr > 0 || !kEarly) load_sp<R, SS>(a.rho, rb, sb, d, se, Vd, v);
         if (rr > 0 && kEarly) load_sp<R, SS>(a.rho, rb, sb, d, so, Vd, vo);
         const bool hold = a.gather && stage_faces;
-        if (a.gather) {
-            auto lnk_e = [&](int mu, cpx<R> *u) { B.link(d, se, mu, u); };
-            face_in(g, nbe, fce, fd, lnk_e, acc);
+        // FP64 unrolls both loops (its register arrays are twice as wide, and
+        // the selects of the rolled form spill there)
+        constexpr int kSiteUnroll = sizeof(R) == 8 ? 2 : 1;
+#pragma unroll kSiteUnroll
+        for (int par = 0; par < 2; par++) {
+            const int s = par ? so : se;
+            cpx<R> t[12];
+            if (kEarly) {
 #pragma unroll
-            for (int k = 0; k < 12; k++) v[k] = v[k] + kappa * acc[k];
-        }
+                for (int k = 0; k < 12; k++) t[k] = par ? vo[k] : v[k];
+            } else if (par) {
+                load_sp<R, SS>(a.rho, rb, sb, d, so, Vd, t);
+            } else {
 #pragma unroll
-        for (int k = 0; k < 12; k++) sR[k * Vh + i] = v[k];
-        if (!kEarly) load_sp<R, SS>(a.rho, rb, sb, d, so, Vd, vo);
-        if (a.gather) {
-            auto lnk_o = [&](int mu, cpx<R> *u) { B.link(d, so, mu, u); };
-            face_in(g, nbo, fco, fd, lnk_o, acc);
+                for (int k = 0; k < 12; k++) t[k] = v[k];
+            }
+            if (a.gather) {
+                uint16_t nb[8];
 #pragma unroll
-            for (int k = 0; k < 12; k++) vo[k] = vo[k] + kappa * acc[k];
+                for (int k = 0; k < 8; k++) nb[k] = par ? nbo[k] : nbe[k];
+                auto lnk = [&](int mu, cpx<R> *u) { B.link(d, s, mu, u); };
+                face_in(g, nb, par ? fco : fce, fd, lnk, acc);
+#pragma unroll
+                for (int k = 0; k < 12; k++) t[k] = t[k] + kappa * acc[k];
+            }
+            if (par == 0) {
+#pragma unroll
+                for (int k = 0; k < 12; k++) sR[k * Vh + i] = t[k];
+            } else {
+#pragma unroll
+                for (int k = 0; k < 12; k++) vo[k] = t[k];
+            }
         }
         if (hold) __syncthreads();
 #pragma unroll
@@ -620,34 +640,46 @@ __global__ void __launch_bounds__(256) k_sap(const SapArgs<R, SL, SC, SS, SP> a)
                     sR[k * Vh + i] = last ? x[k] : r[k];
                 }
                 if (last) store_sp<R, SS>(a.rho, rb, sb, d, se, Vd, r);  // final residual, even site
-            } else if (type == PH_RECON_ODD) {
-                // outputs: the correction pushed across the faces, psi and rho on this domain
-                B.face_out(se, nbe, fce, sNbd, x, a.face + fr);
-                B.face_out(so, nbo, fco, sNbd, c, a.face + fr);
-                if (a.first_psi) {
-                    store_sp<R, SP>(a.psi, rb, sb, d, se, Vd, x);
-                    store_sp<R, SP>(a.psi, rb, sb, d, so, Vd, c);
-                } else {
-                    cpx<R> q[12];
-                    load_sp<R, SP>(a.psi, rb, sb, d, se, Vd, q);
-#pragma unroll
-                    for (int k = 0; k < 12; k++) q[k] = q[k] + x[k];
-                    store_sp<R, SP>(a.psi, rb, sb, d, se, Vd, q);
-                    load_sp<R, SP>(a.psi, rb, sb, d, so, Vd, q);
-#pragma unroll
-                    for (int k = 0; k < 12; k++) q[k] = q[k] + c[k];
-                    store_sp<R, SP>(a.psi, rb, sb, d, so, Vd, q);
-                }
-#pragma unroll
-                for (int k = 0; k < 12; k++) c[k] = mk<R>(0, 0);
-                store_sp<R, SS>(a.rho, rb, sb, d, so, Vd, c);
             } else {
-                // setup-odd / mr-odd: t_o -> sT
+                // setup-odd / mr-odd: t_o -> sT; reconstruction: x_o -> sT
 #pragma unroll
                 for (int k = 0; k < 12; k++) sT[k * Vh + i] = c[k];
             }
             __syncthreads();
         }
+
+        // Outputs of the visit, after the phase loop (kept out of its body so
+        // that the loop stays in the instruction cache): the correction
+        // delta = (x_e in sR, x_o in sT) pushed across the faces, psi += delta,
+        // and the odd residual, now zero.  The even residual was stored by the
+        // last MR step.
+#pragma unroll kSiteUnroll
+        for (int par = 0; par < 2; par++) {
+            const int s = par ? so : se;
+            const cpx<R> *src = par ? sT : sR;
+            cpx<R> dl[12];
+#pragma unroll
+            for (int k = 0; k < 12; k++) dl[k] = src[k * Vh + i];
+            uint16_t nb[8];
+#pragma unroll
+            for (int k = 0; k < 8; k++) nb[k] = par ? nbo[k] : nbe[k];
+            B.face_out(s, nb, par ? fco : fce, sNbd, dl, a.face + fr);
+            if (a.first_psi) {
+                store_sp<R, SP>(a.psi, rb, sb, d, s, Vd, dl);
+            } else {
+                cpx<R> q[12];
+                load_sp<R, SP>(a.psi, rb, sb, d, s, Vd, q);
+#pragma unroll
+                for (int k = 0; k < 12; k++) q[k] = q[k] + dl[k];
+                store_sp<R, SP>(a.psi, rb, sb, d, s, Vd, q);
+            }
+            if (par) {
+#pragma unroll
+                for (int k = 0; k < 12; k++) dl[k] = mk<R>(0, 0);
+                store_sp<R, SS>(a.rho, rb, sb, d, s, Vd, dl);
+            }
+        }
+        if (rr + 1 < a.nrhs) __syncthreads();  // sT and sRo are restaged for the next source
     }
 }
 
