@@ -162,6 +162,24 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def ncu_traffic(kernel):
+    """DRAM bytes per launch of `kernel` on the default workload from one ncu
+    capture (profiles/traffic.json), or None once the kernel's sources have
+    changed since the capture (the record holds their SHA-256)."""
+    import hashlib
+
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f)[kernel]
+        h = hashlib.sha256()
+        for src in rec["sources"]:
+            with open(os.path.join(ROOT, src), "rb") as f:
+                h.update(f.read())
+    except (OSError, KeyError, ValueError):
+        return None
+    return rec["dram_bytes_per_launch"] if h.hexdigest() == rec["sha256"] else None
+
+
 # --------------------------------------------------------------- oracle leg
 
 def oracle_sample(w, U=None):
@@ -348,7 +366,9 @@ def run_qdd(args):
         roof = {"kernel": f"k_sap (Schwarz colour half-sweep, {W['sap_prec']} storage, FP32 arithmetic)"
                 if W["sap_prec"] != "f64" else "k_sap (Schwarz colour half-sweep, FP64)",
                 "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak, "traffic": None, "ms_per_launch": ms_launch, "launches": kt["sap"][1],
+                "frac": achieved / fp32_peak,
+                "traffic": ncu_traffic("k_sap") if args.config == 2 else None,
+                "ms_per_launch": ms_launch, "launches": kt["sap"][1],
                 "flop_per_launch": flop,
                 "peak_source": f"{sm_count} SMs x 128 FP32 lanes x 2 flop x {pk.get('sm_max_mhz', 2070.0):.0f} MHz"}
     elif dom_cls == "dslash":
