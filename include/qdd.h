@@ -83,7 +83,11 @@ typedef struct {
     qdd_prec sap_prec;    /* preconditioner precision */
     qdd_prec arnoldi_prec;/* QDD_PREC_F64, QDD_PREC_DF64 or QDD_PREC_F32: operator
                              in w = D z_j (the restart residual is always FP64) */
-    int use_sap;          /* 0: no preconditioner (plain GMRES) */
+    int use_sap;          /* preconditioner: 0 none (plain GMRES), 1 the
+                             Schwarz method (SAP), 2 the two-level multigrid
+                             V-cycle with the Schwarz smoother (qdd_mg_setup
+                             first; one right-hand side; its own smoother
+                             parameters replace nmr, ncy and sap_prec) */
     int nrhs;             /* right-hand sides solved together (1..12) */
     int reorth;           /* Gram-Schmidt: 0 classical, 1 classical with
                              selective re-orthogonalisation, 2 twice always */
@@ -221,6 +225,58 @@ void qdd_default_params(qdd_solve_params *p);
  */
 qdd_status qdd_solve(qdd_gauge *g, const double *b, double *x, int on_device, const qdd_solve_params *p,
                      qdd_report *rep, void *stream);
+
+/* -------------------------------------------------------------- multigrid */
+
+/*
+ * Two-level aggregation multigrid preconditioner whose smoother is the
+ * Schwarz method (Sec. 2.4 of the paper: the Krylov solver is preconditioned
+ * by a V-cycle with the domain-decomposition preconditioner as smoother; the
+ * paper gives no formula, the construction below is this library's reading).
+ *   aggregates  the gauge field's Schwarz domains, each split by chirality
+ *               (spins {0,1} and {2,3}), so the prolongator commutes with gamma5
+ *   setup       the nv given vectors w_k are each replaced setup_iters times by
+ *               M_SAP w_k (setup_ncy Schwarz cycles of nmr MR steps) and
+ *               normalised; their restrictions to every aggregate-chirality
+ *               block are orthonormalised (modified Gram-Schmidt, twice) and
+ *               become the prolongator's columns P (stored in FP32)
+ *   coarse      D_c = P^H D P, a 9-point stencil of (2 nv) x (2 nv) blocks on
+ *               the lattice of domains (FP32)
+ *   V-cycle     e ~ D_c^{-1} P^H v by one GMRES cycle of coarse_iters steps from
+ *               zero (fewer on an exact breakdown), run on the device without
+ *               host round trips, z = P e, then z += M_SAP(v - D z) with
+ *               post_ncy Schwarz cycles
+ */
+typedef struct {
+    int nv;            /* vectors per aggregate and chirality (1..16) */
+    int setup_iters;   /* smoothing passes over the vectors */
+    int setup_ncy;     /* Schwarz cycles per smoothing pass */
+    int nmr;           /* MR steps per domain visit of the smoother */
+    int post_ncy;      /* Schwarz cycles after the coarse correction (0 = none) */
+    int coarse_iters;  /* steps of the coarse GMRES cycle (1..64) */
+    qdd_prec sap_prec; /* the smoother's precision (as qdd_solve_params) */
+} qdd_mg_params;
+
+/* nv 8, setup_iters 3, setup_ncy 2, nmr 4, post_ncy 2, coarse_iters 12,
+ * FP32 smoother. */
+void qdd_mg_default_params(qdd_mg_params *p);
+
+/* Builds the preconditioner on g (replacing an earlier one).  w0: nv random
+ * spinor fields in the host layout, nv*V*12 complex doubles (host or device
+ * per on_device), read only.  The random numbers are the caller's, so that a
+ * reference implementation can start from the same ones.  Holds
+ * nv*V*96 bytes (P) plus the coarse operator and V-cycle work buffers until
+ * the gauge field is destroyed.  QDD_EINVAL for bad parameters or before
+ * qdd_set_clover. */
+qdd_status qdd_mg_setup(qdd_gauge *g, const qdd_mg_params *p, const double *w0, int on_device);
+
+/* z = M_MG v (one V-cycle) for one spinor in the host layout. */
+qdd_status qdd_mg_vcycle(qdd_gauge *g, const double *v, double *z, int on_device, void *stream);
+
+/* The prolongator's columns as nv spinor fields in the host layout (host
+ * pointer, nv*V*12 complex doubles): field k holds column k of every
+ * aggregate-chirality block. */
+qdd_status qdd_mg_get_basis(qdd_gauge *g, double *out);
 
 /* --------------------------------------------------------- vector algebra */
 

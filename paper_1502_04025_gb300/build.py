@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libqdd.so")
-SOURCES = ["layout.cu", "clover.cu", "dslash.cu", "sap.cu", "blas.cu", "solver.cu", "api.cu", "serve.cu", "tune.cu"]
+SOURCES = ["layout.cu", "clover.cu", "dslash.cu", "sap.cu", "blas.cu", "solver.cu", "api.cu", "serve.cu", "tune.cu", "mg.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

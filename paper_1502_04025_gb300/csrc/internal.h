@@ -190,6 +190,7 @@ struct Gauge {
     DevMem clov64, sclov64;   // FP64 clover A and Schwarz form (A even, A^-1 odd)
     PrecCopy copies[5];       // index = qdd_prec; F64 entry aliases the masters
     std::unique_ptr<Workspace> ws;  // workspace of the synchronous entry points
+    std::shared_ptr<struct Multigrid> mg;  // two-level multigrid preconditioner (qdd_mg_setup)
     std::mutex mu;            // one synchronous call at a time per gauge object
     std::mutex copy_mu;       // guards the lazily built precision copies
     ~Gauge();
@@ -273,6 +274,11 @@ qdd_status blas_axpy_multi(Ctx *ctx, const void *z, bool z_f32, int nvec, int64_
 // out_c (+)= sum_i src_i P[i*ldp + c], c < ncols (P on the device, row-major)
 qdd_status blas_combine(Ctx *ctx, const void *src, bool src_f32, int nsrc, int64_t ld, const double2 *P, int ldp,
                         int ncols, double2 *out, int64_t ldo, int64_t n, int accumulate, cudaStream_t s);
+
+// mg.cu: z = M_MG v, one right-hand side (v FP64, z in zp storage); the
+// precision of the multigrid's Schwarz smoother
+qdd_status mg_vcycle(Gauge *g, const double2 *v, void *z, qdd_prec zp, cudaStream_t s);
+qdd_prec mg_smoother_prec(const Gauge *g);
 
 // solver.cu
 std::unique_ptr<Workspace> make_workspace();

@@ -132,15 +132,21 @@ qdd_status solve_impl(Gauge *g, Workspace *wsp, const double *b_in, double *x_ou
     if (m < 1 || m > 64 || B < 1 || B > 64 || !(p->tol > 0) || p->max_restarts < 0 || p->nmr < 0 || p->ncy < 1 ||
         !is_sap_prec(p->sap_prec) ||
         (p->arnoldi_prec != QDD_PREC_F64 && p->arnoldi_prec != QDD_PREC_F32 && p->arnoldi_prec != QDD_PREC_DF64) ||
-        p->reorth < 0 || p->reorth > 2 || p->dr_k < 0 || p->dr_k >= m) {
+        p->reorth < 0 || p->reorth > 2 || p->dr_k < 0 || p->dr_k >= m || p->use_sap < 0 || p->use_sap > 2) {
         set_error("invalid solve parameters");
+        return QDD_EINVAL;
+    }
+    if (p->use_sap == 2 && (!g->mg || B != 1)) {
+        set_error(g->mg ? "the multigrid preconditioner takes one right-hand side"
+                        : "qdd_mg_setup has not been called");
         return QDD_EINVAL;
     }
     if (!g->have_clover) {
         set_error("set_clover has not been called");
         return QDD_EINVAL;
     }
-    const qdd_prec sp = p->sap_prec;
+    // the preconditioner's storage (the multigrid smoother's, when it is used)
+    const qdd_prec sp = p->use_sap == 2 ? mg_smoother_prec(g) : p->sap_prec;
     const qdd_prec zp = sp == QDD_PREC_F64 ? QDD_PREC_F64 : QDD_PREC_F32;
     if ((p->arnoldi_prec == QDD_PREC_F32 || p->relax_eta > 0) && zp != QDD_PREC_F32) {
         set_error("an FP32 Arnoldi operator needs a single-precision preconditioner output");
@@ -151,7 +157,7 @@ qdd_status solve_impl(Gauge *g, Workspace *wsp, const double *b_in, double *x_ou
         return QDD_EINVAL;
     }
     Workspace &w = *wsp;
-    QDD_TRY(ensure_ws(g, w, m, B, sp, p->use_sap != 0, p->dr_k));
+    QDD_TRY(ensure_ws(g, w, m, B, sp, p->use_sap == 1, p->dr_k));
     if (p->use_sap) QDD_TRY(ensure_copy(g, sp, s));
     if (p->arnoldi_prec != QDD_PREC_F64) QDD_TRY(ensure_copy(g, p->arnoldi_prec, s));
     if (p->relax_eta > 0) QDD_TRY(ensure_copy(g, QDD_PREC_F32, s));
@@ -361,7 +367,9 @@ qdd_status solve_impl(Gauge *g, Workspace *wsp, const double *b_in, double *x_ou
             double2 *wv = V + (int64_t)(j + 1) * ldV;
             char *zj = Z + (size_t)j * n * B * zb;
             // z_j = M v_j
-            if (p->use_sap) {
+            if (p->use_sap == 2) {
+                QDD_TRY(mg_vcycle(g, vj, zj, zp, s));
+            } else if (p->use_sap) {
                 QDD_TRY(launch_spinor_convert(g, vj, nullptr, QDD_PREC_F64, w.rho.p, w.rho_s.as<float>(),
                                               spinor_store(sp), B, s));
                 sb.psi = zj;

@@ -50,6 +50,12 @@ class qdd_report(ctypes.Structure):
         return d
 
 
+class qdd_mg_params(ctypes.Structure):
+    _fields_ = [("nv", ctypes.c_int), ("setup_iters", ctypes.c_int), ("setup_ncy", ctypes.c_int),
+                ("nmr", ctypes.c_int), ("post_ncy", ctypes.c_int), ("coarse_iters", ctypes.c_int),
+                ("sap_prec", ctypes.c_int)]
+
+
 class qdd_tune_result(ctypes.Structure):
     _fields_ = [("dom", ctypes.c_int * 4), ("nmr", ctypes.c_int),
                 ("iters", ctypes.c_int), ("n_tried", ctypes.c_int), ("ms", ctypes.c_double),
@@ -90,6 +96,10 @@ _SIGS = {
                                   ctypes.POINTER(ctypes.c_uint64)]),
     "qdd_poll": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.POINTER(qdd_report), ctypes.c_double]),
     "qdd_serve_config": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "qdd_mg_default_params": (None, [ctypes.POINTER(qdd_mg_params)]),
+    "qdd_mg_setup": (ctypes.c_int, [_vp, ctypes.POINTER(qdd_mg_params), _vp, ctypes.c_int]),
+    "qdd_mg_vcycle": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp]),
+    "qdd_mg_get_basis": (ctypes.c_int, [_vp, _vp]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -346,3 +356,34 @@ def qdd_poll(ctx, ticket: int, timeout_s: float = 0.0):
     if st == QDD_ENOTREADY:
         return st, None
     return st, rep.as_dict()
+
+
+# ------------------------------------------------------------------ multigrid
+
+def qdd_mg_default_params(**kw) -> qdd_mg_params:
+    p = qdd_mg_params()
+    _lib.qdd_mg_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, _prec(v) if k == "sap_prec" else v)
+    return p
+
+
+def qdd_mg_setup(g, w0, params: qdd_mg_params | None = None, **kw):
+    """Build the two-level multigrid preconditioner from the nv random fields w0 (nv, V, 4, 3)."""
+    p = params if params is not None else qdd_mg_default_params(**kw)
+    pw, dev = _ptr(w0)
+    _check(_lib.qdd_mg_setup(g, ctypes.byref(p), pw, dev), "qdd_mg_setup")
+
+
+def qdd_mg_vcycle(g, v):
+    z = _like(v)
+    pv, dev = _ptr(v)
+    pz, _ = _ptr(z)
+    _check(_lib.qdd_mg_vcycle(g, pv, pz, dev, _stream(v)), "qdd_mg_vcycle")
+    return z
+
+
+def qdd_mg_get_basis(g, nv: int, V: int) -> np.ndarray:
+    out = np.empty((nv, V, 4, 3), dtype=np.complex128)
+    _check(_lib.qdd_mg_get_basis(g, out.ctypes.data_as(_vp)), "qdd_mg_get_basis")
+    return out
