@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--serve", action="store_true", help="run the serving mix instead of single solves")
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--op-bench", action="store_true", help="time only the full-lattice operator")
+    ap.add_argument("--mg", action="store_true",
+                    help="time-to-solution near the critical kappa: Schwarz-only against the two-level multigrid")
     ap.add_argument("--op-lattice", default="32,32,32,64")
     ap.add_argument("--op-precs", default="f32,h16,f16,df64,f64")
     ap.add_argument("--op-iters", type=int, default=20)
@@ -511,6 +513,77 @@ def run_op_bench(args):
     qdd.qdd_destroy(ctx)
 
 
+# ------------------------------------------------------------ multigrid
+
+MGW = dict(L=(16, 16, 16, 32), dom=(8, 4, 4, 4), eps=0.5, csw=1.0, kappa=0.143, gauge_seed=1002, source_seed=2002,
+           w0_seed=4001, nv=12, setup_iters=6, setup_ncy=4, nmr=4, post_ncy=4, coarse_iters=12, ncy=4, m=16,
+           tol=1e-10)
+
+
+def run_mg_bench(args):
+    """The same near-critical system solved with Schwarz-preconditioned FGMRES
+    and with FGMRES preconditioned by the two-level multigrid V-cycle (Schwarz
+    smoother): time to a 1e-10 true residual, event-timed, L2 flushed before
+    every solve; the multigrid setup is timed separately."""
+    import torch
+
+    from paper_1502_04025_gb300 import build, inputs
+
+    build.build()
+    from paper_1502_04025_gb300 import qdd
+
+    W = MGW
+    ctx = qdd.qdd_create(0, 0)
+    U = inputs.gauge_field(W["L"], W["eps"], W["gauge_seed"])
+    g = qdd.qdd_create_gauge_field(ctx, W["L"], W["dom"], U)
+    del U
+    qdd.qdd_set_clover(g, W["csw"], W["kappa"])
+    b = torch.from_numpy(inputs.gaussian_source(W["L"], W["source_seed"])).cuda()
+    w0 = torch.from_numpy(inputs.gaussian_source(W["L"], W["w0_seed"], nrhs=W["nv"])).cuda()
+    x = torch.empty_like(b)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    common = dict(tol=W["tol"], restart_m=W["m"], max_restarts=200, arnoldi_prec="df64", relax_eta=1e-6, reorth=0)
+
+    def timed(fn, steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ms, rep = [], None
+        for _ in range(steps):
+            flush.fill_(1.0)
+            e0.record(stream)
+            rep = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms), rep
+
+    p_sap = qdd.qdd_default_params(use_sap=1, nmr=W["nmr"], ncy=W["ncy"], sap_prec="f32", **common)
+    p_mg = qdd.qdd_default_params(use_sap=2, **common)
+    mg_kw = dict(nv=W["nv"], setup_iters=W["setup_iters"], setup_ncy=W["setup_ncy"], nmr=W["nmr"],
+                 post_ncy=W["post_ncy"], coarse_iters=W["coarse_iters"], sap_prec="f32")
+    setup_ms, _ = timed(lambda: qdd.qdd_mg_setup(g, w0, **mg_kw), 1 + max(args.warmup, 1))
+    timed(lambda: qdd.qdd_solve(g, b, p_sap, x=x)[1], args.warmup)
+    ms_sap, r_sap = timed(lambda: qdd.qdd_solve(g, b, p_sap, x=x)[1], args.steps)
+    timed(lambda: qdd.qdd_solve(g, b, p_mg, x=x)[1], args.warmup)
+    ms_mg, r_mg = timed(lambda: qdd.qdd_solve(g, b, p_mg, x=x)[1], args.steps)
+    line = {"metric": "time to a 1e-10 residual near the critical kappa: Schwarz against two-level multigrid",
+            "unit": "ms", "higher_is_better": False, "steps": args.steps, "warmup": args.warmup,
+            "data": "synthetic",
+            "config": {"workload": (f"16^3x32 Wilson-clover, c_sw {W['csw']}, kappa {W['kappa']}, eps {W['eps']} "
+                                    f"links, 8x4x4x4 domains/aggregates, FGMRES({W['m']}), tol {W['tol']}"),
+                       "multigrid": {k: W[k] for k in ("nv", "setup_iters", "setup_ncy", "nmr", "post_ncy",
+                                                       "coarse_iters")},
+                       "schwarz": {"ncy": W["ncy"], "nmr": W["nmr"], "prec": "f32"},
+                       "l2": "256 MB buffer written before every solve"},
+            "schwarz": {"ms": ms_sap, "iters": r_sap["iters"], "true_rel_res": r_sap["true_rel_res"]},
+            "multigrid": {"ms": ms_mg, "iters": r_mg["iters"], "true_rel_res": r_mg["true_rel_res"],
+                          "setup_ms": setup_ms},
+            "speedup": ms_sap / ms_mg}
+    print(json.dumps(line), flush=True)
+    qdd.qdd_destroy_gauge(g)
+    qdd.qdd_destroy(ctx)
+
+
 # ---------------------------------------------------------------- serving
 
 SERVE_LATTICES = [((8, 8, 8, 8), (4, 4, 4, 4)), ((16, 16, 16, 32), (8, 4, 4, 4)),
@@ -637,6 +710,8 @@ def main():
         run_serve(args)
     elif args.op_bench:
         run_op_bench(args)
+    elif args.mg:
+        run_mg_bench(args)
     else:
         run_qdd(args)
 
