@@ -82,6 +82,7 @@ def parse():
     ap.add_argument("--impl", choices=["qdd", "reference"], default="qdd")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-dslash", action="store_true")
+    ap.add_argument("--no-fp64-compare", action="store_true", help="skip the plain FP64 path on the same system")
     ap.add_argument("--e2e-steps", type=int, default=3)
     return ap.parse_args()
 
@@ -405,6 +406,47 @@ def run_qdd(args):
     if rank == 0 and args.config != 2 and e2e_ms:
         parity = sampled_residual(W, U, b, xh)
 
+    # ---- batching: the same sources one at a time (the first source's solve, times nrhs)
+    unbatched = None
+    if rank == 0 and nrhs > 1:
+        p1 = qdd.qdd_default_params(tol=W["tol"], restart_m=W["m"], nmr=W["nmr"], ncy=W["ncy"],
+                                    sap_prec=W["sap_prec"], arnoldi_prec=W["arnoldi_prec"], max_restarts=200,
+                                    nrhs=1, relax_eta=W.get("relax_eta", 0.0), reorth=W.get("reorth", 1))
+        b1 = bd[0].contiguous()
+        x1 = torch.empty_like(b1)
+        qdd.qdd_solve(g, b1, p1, x=x1, allow_noconv=True)
+        ms1 = []
+        for _ in range(2):
+            flush.fill_(1.0)
+            e0.record(stream)
+            _, r1 = qdd.qdd_solve(g, b1, p1, x=x1, allow_noconv=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms1.append(e0.elapsed_time(e1))
+        t1 = statistics.median(ms1)
+        unbatched = {"one_source_ms": t1, "iters": r1["iters"], "nrhs_times_one_ms": t1 * nrhs,
+                     "gain_of_batching": t1 * nrhs / ms_step}
+
+    # ---- the same system with FP64 throughout (Schwarz preconditioner and
+    # Arnoldi operator): the plain FP64 GPU path the mixed-precision one is
+    # measured against
+    plain = None
+    if rank == 0 and args.config == 2 and not args.no_fp64_compare:
+        p64 = qdd.qdd_default_params(tol=W["tol"], restart_m=W["m"], nmr=W["nmr"], ncy=W["ncy"], sap_prec="f64",
+                                     arnoldi_prec="f64", max_restarts=200, nrhs=nrhs, reorth=1)
+        qdd.qdd_solve(g, bd, p64, x=xd, allow_noconv=True)
+        ms64 = []
+        for _ in range(2):
+            flush.fill_(1.0)
+            e0.record(stream)
+            _, r64 = qdd.qdd_solve(g, bd, p64, x=xd, allow_noconv=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms64.append(e0.elapsed_time(e1))
+        plain = {"ms": statistics.median(ms64), "iters": r64["iters"], "true_rel_res": r64["true_rel_res"],
+                 "converged": bool(r64["converged"]), "speedup_of_mixed": statistics.median(ms64) / ms_step,
+                 "params": "FP64 Schwarz (nmr 4, ncy 4), FP64 Arnoldi operator, re-orthogonalised Gram-Schmidt"}
+
     # ---- full-lattice operator throughput (FP32 and FP16 storage) on a lattice > L2
     dslash = None
     if not args.no_dslash and rank == 0 and args.config == 2:
@@ -459,7 +501,7 @@ def run_qdd(args):
                 "iters": last["iters"], "restarts": last["restarts"], "true_rel_res": last["true_rel_res"],
                 "converged": bool(last["converged"]),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-                "dslash": dslash}
+                "dslash": dslash, "plain_fp64": plain, "unbatched": unbatched}
         if parity is not None:
             line["parity"] = parity
         print(json.dumps(line), flush=True)
