@@ -226,7 +226,7 @@ __device__ __forceinline__ void hop_df_rt(const HopSpin &hs, const cdf *U, const
 }
 
 template <typename SI>
-__global__ void __launch_bounds__(128) k_dslash_df(Geom g, const float4 *U, const float4 *A,
+__global__ void __launch_bounds__(128, 4) k_dslash_df(Geom g, const float4 *U, const float4 *A,
                                                    const typename SI::T2 *in, double2 *out, df kappa)
 {
     int gi = blockIdx.x * blockDim.x + threadIdx.x;
