@@ -96,6 +96,20 @@ def peaks():
         return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def op_bytes_per_site(prec, three_rows=True):
+    """Algorithmic bytes of one full-lattice operator apply per site: links
+    (4 per site, whole or their first two rows), the two clover blocks, the
+    input spinor and the output, each read or written once; 16-bit fields
+    carry one FP32 scale per site."""
+    rows = 3 if three_rows or prec in ("f64", "df64") else 2
+    if prec in ("f64", "df64"):
+        return 4 * 9 * 16 + 36 * 16 + 2 * 12 * 16  # df64 splits FP64 values into FP32 pairs: the same bytes
+    link = 4 * rows * 3 * (8 if prec == "f32" else 4)
+    clover = 36 * 8 if prec == "f32" else 36 * 4 + 4
+    spinor = 12 * 8 if prec in ("f32", "h16") else 12 * 4 + 4
+    return link + clover + 2 * spinor
+
+
 def crossing_hops_per_site(dom):
     """Average number of hops per site that leave a domain: 2 faces per
     direction, each holding Vd/dom[mu] sites."""
@@ -458,8 +472,14 @@ def run_qdd(args):
         xs = torch.from_numpy(inputs.gaussian_source(DSL["L"], DSL["source_seed"])).cuda()
         ys = torch.empty_like(xs)
         Vl = int(np.prod(DSL["L"]))
-        dslash = {"lattice": list(DSL["L"]), "flop_per_site": 1848}
-        for prec, bps in (("f32", 768), ("h16", 484), ("f16", 392), ("df64", 1536), ("f64", 1536)):
+        two_rows, _ = qdd.qdd_link_compression(gd)
+        dslash = {"lattice": list(DSL["L"]), "flop_per_site": 1848,
+                  "link_rows": 2 if two_rows else 3}
+        for name in ("f32", "f32_three_rows", "h16", "f16", "df64", "f64"):
+            prec = name.split("_")[0]
+            rows3 = name.endswith("three_rows") or not two_rows
+            qdd.qdd_set_link_compression(gd, not rows3)
+            bps = op_bytes_per_site(prec, rows3)
             for _ in range(3):
                 qdd.qdd_apply_D(gd, xs, prec, out=ys)
             qdd.qdd_set_profiling(ctx, qdd.QDD_PROF_DSLASH)
@@ -469,10 +489,11 @@ def run_qdd(args):
             kd = qdd.qdd_get_kernel_times(ctx, reset=True)
             qdd.qdd_set_profiling(ctx, 0)
             ms = kd["dslash"][0] / kd["dslash"][1]
-            dslash[prec] = {"ms": ms, "gflops": 1848 * Vl / (ms * 1e-3) / 1e9,
+            dslash[name] = {"ms": ms, "gflops": 1848 * Vl / (ms * 1e-3) / 1e9,
                             "gbs": bps * Vl / (ms * 1e-3) / 1e9,
                             "frac_hbm": bps * Vl / (ms * 1e-3) / 1e9 / pk["hbm_gbs"],
                             "bytes_per_site": bps}
+        qdd.qdd_set_link_compression(gd, two_rows)
         qdd.qdd_destroy_gauge(gd)
         U = None
 
@@ -536,7 +557,8 @@ def run_op_bench(args):
     out = {"metric": "Wilson-clover Dslash throughput", "unit": "GFLOP/s", "lattice": list(L),
            "domain": list(DSL["dom"]), "flop_per_site": 1848, "peak_hbm_gbs": pk["hbm_gbs"],
            "peak_kind": "of measured" if pk_kind == "measured" else "of fallback"}
-    bps_of = {"f32": 768, "h16": 484, "f16": 392, "bf16": 392, "df64": 1536, "f64": 1536}
+    two_rows, _ = qdd.qdd_link_compression(g)
+    out["link_rows"] = 2 if two_rows else 3
     for prec in args.op_precs.split(","):
         for _ in range(3):
             qdd.qdd_apply_D(g, xs, prec, out=ys)
@@ -547,7 +569,7 @@ def run_op_bench(args):
         kd = qdd.qdd_get_kernel_times(ctx, reset=True)
         qdd.qdd_set_profiling(ctx, 0)
         ms = kd["dslash"][0] / kd["dslash"][1]
-        bps = bps_of[prec]
+        bps = op_bytes_per_site(prec, not two_rows)
         out[prec] = {"ms": ms, "gflops": 1848 * Vl / (ms * 1e-3) / 1e9, "gbs": bps * Vl / (ms * 1e-3) / 1e9,
                      "frac_hbm": bps * Vl / (ms * 1e-3) / 1e9 / pk["hbm_gbs"], "bytes_per_site": bps}
     print(json.dumps(out), flush=True)

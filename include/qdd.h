@@ -171,6 +171,22 @@ qdd_status qdd_create_gauge_field(qdd_ctx *ctx, const int L[4], const int dom[4]
 void qdd_destroy_gauge(qdd_gauge *g);
 
 /*
+ * Two-row link storage for the full-lattice operator in FP32, FP16 and BF16
+ * (not part of the paper, which stores whole links): an SU(3) link's third
+ * row is the complex conjugate of the cross product of its first two (the
+ * cofactors of a unitary matrix of determinant 1), so those operators read
+ * 6 of the 9 entries and rebuild the rest, 96 of 288 bytes per site fewer in
+ * FP32.  At creation every link is checked on the device (max |U U^+ - 1|
+ * and |det U - 1| <= 1e-10); when all pass, two-row storage is on.
+ * qdd_set_link_compression(g, 0) switches it off; (g, 1) switches it back
+ * on and returns QDD_EINVAL for a field that failed the check.  The FP64
+ * and double-float operators and the Schwarz kernel read whole links.
+ * qdd_link_compression reports the setting and the check's outcome.
+ */
+qdd_status qdd_set_link_compression(qdd_gauge *g, int two_rows);
+qdd_status qdd_link_compression(qdd_gauge *g, int *two_rows, int *is_su3);
+
+/*
  * Build the clover term A = 1 + i kappa c_sw sum sigma F (two Hermitian 6x6
  * chirality blocks per site) and the inverse blocks on odd sites used by the
  * even-odd domain solver (Sec. 3.1, footnote on the domain inversion).  Must

@@ -191,6 +191,22 @@ qdd_status ensure_copy(Gauge *g, qdd_prec prec, cudaStream_t s)
     return QDD_OK;
 }
 
+qdd_status ensure_links12(Gauge *g, qdd_prec prec, cudaStream_t s)
+{
+    prec = field_store(prec);
+    if (prec != QDD_PREC_F32 && prec != QDD_PREC_F16S && prec != QDD_PREC_BF16S) {
+        set_error("two-row links exist for FP32, FP16 and BF16 storage only");
+        return QDD_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(g->copy_mu);
+    PrecCopy &c = g->copies[prec];
+    if (c.valid12) return QDD_OK;
+    QDD_TRY(c.links12.ensure(g->ctx, (size_t)g->hg.V * 24 * elem_bytes(prec)));
+    QDD_TRY(launch_links12_convert(g, prec, c.links12.p, s));
+    c.valid12 = true;
+    return QDD_OK;
+}
+
 // per-gauge staging buffers for the entry points that are not the solver
 struct Staging {
     DevMem io, a, a_s, b, b_s, c, c_s, err;
@@ -367,6 +383,14 @@ qdd_status qdd_create_gauge_field(qdd_ctx *ctx, const int L[4], const int dom[4]
         src = tmp.as<double>();
     }
     QDD_TRY(launch_links_to_internal(g.get(), src, 0));
+    // SU(3) links (to rounding) let the full-lattice operator read two rows per link
+    DevMem bad;
+    QDD_TRY(bad.alloc(ctx, sizeof(int)));
+    QDD_TRY(launch_su3_check(g.get(), kSu3Tol, bad.as<int>(), 0));
+    int h_bad = 1;
+    QDD_CUDA(cudaMemcpy(&h_bad, bad.p, sizeof(int), cudaMemcpyDeviceToHost));
+    g->su3 = h_bad == 0;
+    g->two_rows = g->su3;
     QDD_CUDA(cudaDeviceSynchronize());
     ctx->timer.resolve();
     *out = g.release();
@@ -379,6 +403,34 @@ void qdd_destroy_gauge(qdd_gauge *g)
     cudaSetDevice(g->ctx->device);
     cudaDeviceSynchronize();
     delete g;
+}
+
+qdd_status qdd_set_link_compression(qdd_gauge *g, int two_rows)
+{
+    clear_error();
+    if (!g || (two_rows != 0 && two_rows != 1)) {
+        set_error("invalid argument");
+        return QDD_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(g->mu);
+    if (two_rows && !g->su3) {
+        set_error("links are not SU(3) to %g: the third row cannot be rebuilt from the first two", kSu3Tol);
+        return QDD_EINVAL;
+    }
+    g->two_rows = two_rows != 0;
+    return QDD_OK;
+}
+
+qdd_status qdd_link_compression(qdd_gauge *g, int *two_rows, int *is_su3)
+{
+    clear_error();
+    if (!g || !two_rows || !is_su3) {
+        set_error("null argument");
+        return QDD_EINVAL;
+    }
+    *two_rows = g->two_rows ? 1 : 0;
+    *is_su3 = g->su3 ? 1 : 0;
+    return QDD_OK;
 }
 
 qdd_status qdd_set_clover(qdd_gauge *g, double c_sw, double kappa)

@@ -30,15 +30,27 @@ __device__ __forceinline__ void load_spinor(const Field<S> &f, int64_t gi_plane_
     }
 }
 
-template <typename R, typename S>
+// Link U_mu of site s of domain d.  L12: the field holds the first two rows
+// (24 planes per site) and the third is rebuilt as the conjugated cross
+// product of the two, i.e. from the cofactors of U = (U^+)^-1 for det U = 1.
+template <typename R, typename S, bool L12>
 __device__ __forceinline__ void load_link(const Field<S> &U, int d, int s, int mu, int Vd, cpx<R> *u)
 {
-    const typename S::T2 *p = U.p + ((int64_t)d * 36 + mu * 9) * Vd + s;
+    if (L12) {
+        const typename S::T2 *p = U.p + ((int64_t)d * 24 + mu * 6) * Vd + s;
 #pragma unroll
-    for (int k = 0; k < 9; k++) u[k] = ld_c<R>(p + (int64_t)k * Vd);
+        for (int k = 0; k < 6; k++) u[k] = ld_c<R>(p + (int64_t)k * Vd);
+        u[6] = conj(u[1] * u[5] - u[2] * u[4]);
+        u[7] = conj(u[2] * u[3] - u[0] * u[5]);
+        u[8] = conj(u[0] * u[4] - u[1] * u[3]);
+    } else {
+        const typename S::T2 *p = U.p + ((int64_t)d * 36 + mu * 9) * Vd + s;
+#pragma unroll
+        for (int k = 0; k < 9; k++) u[k] = ld_c<R>(p + (int64_t)k * Vd);
+    }
 }
 
-template <int MU, typename R, typename SL, typename SI>
+template <int MU, typename R, typename SL, typename SI, bool L12>
 __device__ __forceinline__ void dslash_dir(const Geom &g, const Field<SL> &U, const Field<SI> &in, int64_t rbase,
                                            int64_t sbase, int d, int s, cpx<R> *acc)
 {
@@ -48,7 +60,7 @@ __device__ __forceinline__ void dslash_dir(const Geom &g, const Field<SL> &U, co
         int nd = (e & kCross) ? __ldg(g.nbd + d * 8 + 2 * MU) : d;
         int ns = e & kSlotMask;
         load_spinor<R, SI>(in, rbase + (int64_t)nd * 12 * g.Vd + ns, sbase + (int64_t)nd * g.Vd + ns, g.Vd, x);
-        load_link<R, SL>(U, d, s, MU, g.Vd, u);
+        load_link<R, SL, L12>(U, d, s, MU, g.Vd, u);
         hop<MU, +1>(u, x, acc);
     }
     {
@@ -56,12 +68,12 @@ __device__ __forceinline__ void dslash_dir(const Geom &g, const Field<SL> &U, co
         int nd = (e & kCross) ? __ldg(g.nbd + d * 8 + 2 * MU + 1) : d;
         int ns = e & kSlotMask;
         load_spinor<R, SI>(in, rbase + (int64_t)nd * 12 * g.Vd + ns, sbase + (int64_t)nd * g.Vd + ns, g.Vd, x);
-        load_link<R, SL>(U, nd, ns, MU, g.Vd, u);
+        load_link<R, SL, L12>(U, nd, ns, MU, g.Vd, u);
         hop<MU, -1>(u, x, acc);
     }
 }
 
-template <typename R, typename SL, typename SC, typename SI, typename SO, bool RESID>
+template <typename R, typename SL, typename SC, typename SI, typename SO, bool RESID, bool L12>
 __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 1) k_dslash(Geom g, Field<SL> U, Field<SC> A, Field<SI> in, Field<SO> out,
                                                 const double2 *b, R kappa)
 {
@@ -75,10 +87,10 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 1) k_dslash(Geom g, 
     cpx<R> acc[12];
 #pragma unroll
     for (int k = 0; k < 12; k++) acc[k] = mk<R>(0, 0);
-    dslash_dir<0, R, SL, SI>(g, U, in, rbase, sbase, d, s, acc);
-    dslash_dir<1, R, SL, SI>(g, U, in, rbase, sbase, d, s, acc);
-    dslash_dir<2, R, SL, SI>(g, U, in, rbase, sbase, d, s, acc);
-    dslash_dir<3, R, SL, SI>(g, U, in, rbase, sbase, d, s, acc);
+    dslash_dir<0, R, SL, SI, L12>(g, U, in, rbase, sbase, d, s, acc);
+    dslash_dir<1, R, SL, SI, L12>(g, U, in, rbase, sbase, d, s, acc);
+    dslash_dir<2, R, SL, SI, L12>(g, U, in, rbase, sbase, d, s, acc);
+    dslash_dir<3, R, SL, SI, L12>(g, U, in, rbase, sbase, d, s, acc);
 
     cpx<R> x[12];
     load_spinor<R, SI>(in, rbase + (int64_t)d * 12 * g.Vd + s, sbase + gi, g.Vd, x);
@@ -302,7 +314,7 @@ __global__ void __launch_bounds__(128, 4) k_dslash_df(Geom g, const float4 *U, c
     }
 }
 
-template <typename R, typename SL, typename SC, typename SI, typename SO, bool RESID>
+template <typename R, typename SL, typename SC, typename SI, typename SO, bool RESID, bool L12 = false>
 static qdd_status run_dslash(Gauge *g, Field<SL> U, Field<SC> A, const void *in, const float *in_s, void *out,
                              float *out_s, const double2 *b, int nrhs, cudaStream_t s)
 {
@@ -310,9 +322,24 @@ static qdd_status run_dslash(Gauge *g, Field<SL> U, Field<SC> A, const void *in,
     Field<SO> fo{(typename SO::T2 *)out, out_s};
     dim3 grid((g->hg.V + 127) / 128, nrhs);
     LaunchScope ls(g->ctx->timer, K_DSLASH, s);
-    k_dslash<R, SL, SC, SI, SO, RESID><<<grid, 128, 0, s>>>(g->geom, U, A, fi, fo, b, (R)g->kappa);
+    k_dslash<R, SL, SC, SI, SO, RESID, L12><<<grid, 128, 0, s>>>(g->geom, U, A, fi, fo, b, (R)g->kappa);
     QDD_CUDA(cudaGetLastError());
     return QDD_OK;
+}
+
+// FP32 arithmetic on links of storage SL: the two-row copy when the gauge
+// field allows it, else whole links
+template <typename SL, typename SC, typename SI, typename SO>
+static qdd_status run_dslash_lowp(Gauge *g, qdd_prec fp, Field<SC> A, const void *in, const float *in_s, void *out,
+                                  float *out_s, int nrhs, cudaStream_t s)
+{
+    if (g->two_rows) {
+        QDD_TRY(ensure_links12(g, fp, s));
+        Field<SL> U{(typename SL::T2 *)g->copies[fp].links12.p, nullptr};
+        return run_dslash<float, SL, SC, SI, SO, false, true>(g, U, A, in, in_s, out, out_s, nullptr, nrhs, s);
+    }
+    Field<SL> U{(typename SL::T2 *)g->copies[fp].links.p, nullptr};
+    return run_dslash<float, SL, SC, SI, SO, false, false>(g, U, A, in, in_s, out, out_s, nullptr, nrhs, s);
 }
 
 qdd_status launch_dslash(Gauge *g, qdd_prec arith, qdd_prec fp, const void *in, const float *in_s, qdd_prec ip,
@@ -360,31 +387,25 @@ qdd_status launch_dslash(Gauge *g, qdd_prec arith, qdd_prec fp, const void *in, 
         PrecCopy &c = g->copies[fp];
         switch (fp) {
         case QDD_PREC_F32: {
-            Field<StF32> U{c.links.as<float2>(), nullptr}, A{c.clov.as<float2>(), nullptr};
+            Field<StF32> A{c.clov.as<float2>(), nullptr};
             if (ip == QDD_PREC_F32 && op == QDD_PREC_F32)
-                return run_dslash<float, StF32, StF32, StF32, StF32, false>(g, U, A, in, in_s, out, out_s, b, nrhs,
-                                                                            s);
+                return run_dslash_lowp<StF32, StF32, StF32, StF32>(g, fp, A, in, in_s, out, out_s, nrhs, s);
             if (ip == QDD_PREC_F32 && op == QDD_PREC_F64)
-                return run_dslash<float, StF32, StF32, StF32, StF64, false>(g, U, A, in, in_s, out, out_s, b, nrhs,
-                                                                            s);
+                return run_dslash_lowp<StF32, StF32, StF32, StF64>(g, fp, A, in, in_s, out, out_s, nrhs, s);
             break;
         }
         case QDD_PREC_F16S: {
-            Field<StF16> U{c.links.as<__half2>(), nullptr}, A{c.clov.as<__half2>(), c.clov_s.as<float>()};
+            Field<StF16> A{c.clov.as<__half2>(), c.clov_s.as<float>()};
             if (ip == QDD_PREC_F16S && op == QDD_PREC_F16S)
-                return run_dslash<float, StF16, StF16, StF16, StF16, false>(g, U, A, in, in_s, out, out_s, b, nrhs,
-                                                                            s);
+                return run_dslash_lowp<StF16, StF16, StF16, StF16>(g, fp, A, in, in_s, out, out_s, nrhs, s);
             if (ip == QDD_PREC_F32 && op == QDD_PREC_F32)  // half links/clover, single spinors
-                return run_dslash<float, StF16, StF16, StF32, StF32, false>(g, U, A, in, in_s, out, out_s, b, nrhs,
-                                                                            s);
+                return run_dslash_lowp<StF16, StF16, StF32, StF32>(g, fp, A, in, in_s, out, out_s, nrhs, s);
             break;
         }
         case QDD_PREC_BF16S: {
-            Field<StBF16> U{c.links.as<__nv_bfloat162>(), nullptr},
-                A{c.clov.as<__nv_bfloat162>(), c.clov_s.as<float>()};
+            Field<StBF16> A{c.clov.as<__nv_bfloat162>(), c.clov_s.as<float>()};
             if (ip == QDD_PREC_BF16S && op == QDD_PREC_BF16S)
-                return run_dslash<float, StBF16, StBF16, StBF16, StBF16, false>(g, U, A, in, in_s, out, out_s, b,
-                                                                                nrhs, s);
+                return run_dslash_lowp<StBF16, StBF16, StBF16, StBF16>(g, fp, A, in, in_s, out, out_s, nrhs, s);
             break;
         }
         default: break;

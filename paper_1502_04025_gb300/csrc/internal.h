@@ -161,6 +161,8 @@ qdd_status make_geometry(const int L[4], const int dom[4], HostGeom &hg);
 struct PrecCopy {
     bool valid = false;
     DevMem links, clov, clov_s, sclov, sclov_s;
+    bool valid12 = false;
+    DevMem links12;  // first two rows of each link, for the full-lattice operator
 };
 
 // Device and pinned host buffers of one solve (Krylov basis, preconditioner
@@ -185,6 +187,8 @@ struct Gauge {
     Geom geom{};
     DevMem d_nbl, d_nbd, d_site_of, d_block_slot, d_fcoord;
     DevMem links64;           // FP64 links, internal layout
+    bool su3 = false;         // every link SU(3) to kSu3Tol
+    bool two_rows = false;    // the FP32/16-bit full-lattice operator reads two rows per link
     bool have_clover = false;
     double csw = 0, kappa = 0;
     DevMem clov64, sclov64;   // FP64 clover A and Schwarz form (A even, A^-1 odd)
@@ -203,6 +207,10 @@ struct Fields {
 };
 
 qdd_status ensure_copy(Gauge *g, qdd_prec prec, cudaStream_t s);
+// the two-row link copy of a storage precision (FP32, FP16, BF16)
+qdd_status ensure_links12(Gauge *g, qdd_prec prec, cudaStream_t s);
+// links whose unitarity and determinant deviate by more than this keep three rows
+constexpr double kSu3Tol = 1e-10;
 
 // storage of the spinors and of the links/clover copy a precision mode uses
 inline qdd_prec spinor_store(qdd_prec p) { return p == QDD_PREC_H16 ? QDD_PREC_F32 : p; }
@@ -228,6 +236,9 @@ qdd_status launch_spinor_convert(Gauge *g, const void *src, const float *src_sca
 qdd_status launch_links_convert(Gauge *g, qdd_prec dp, void *dst, cudaStream_t s);
 qdd_status launch_clover_convert(Gauge *g, const double2 *src, qdd_prec dp, void *dst, float *dst_scale,
                                  cudaStream_t s);
+// *d_bad = 1 when some link is not SU(3) to tol; two-row copy of the links
+qdd_status launch_su3_check(Gauge *g, double tol, int *d_bad, cudaStream_t s);
+qdd_status launch_links12_convert(Gauge *g, qdd_prec dp, void *dst, cudaStream_t s);
 // FP64 complex -> double-float (hi, lo) pairs
 qdd_status launch_split_convert(Gauge *g, const double2 *src, float4 *dst, int64_t n, cudaStream_t s);
 

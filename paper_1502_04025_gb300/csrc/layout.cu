@@ -277,6 +277,49 @@ __global__ void k_split_convert(int64_t n, const double2 *src, float4 *dst)
     dst[i] = make_float4(rh, __double2float_rn(a.x - (double)rh), ih, __double2float_rn(a.y - (double)ih));
 }
 
+// Sets *bad when a link is not SU(3) to tol: max |(U U^+ - 1)_ij| or |det U - 1|.
+// One thread per link (domain d, direction mu, site s).
+__global__ void k_su3_check(Geom g, const double2 *U, double tol, int *bad)
+{
+    const int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (li >= (int64_t)g.V * 4) return;
+    const int64_t d = li / (4 * g.Vd);
+    const int mu = (int)((li / g.Vd) % 4), s = (int)(li % g.Vd);
+    const double2 *p = U + (d * 36 + mu * 9) * g.Vd + s;
+    cpx<double> u[9];
+    for (int k = 0; k < 9; k++) {
+        double2 a = __ldg(p + (int64_t)k * g.Vd);
+        u[k] = mk(a.x, a.y);
+    }
+    double dev = 0;
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+            cpx<double> t = mk(i == j ? -1.0 : 0.0, 0.0);
+            for (int k = 0; k < 3; k++) t = t + u[i * 3 + k] * conj(u[j * 3 + k]);
+            dev = fmax(dev, fmax(fabs(t.re), fabs(t.im)));
+        }
+    cpx<double> det = u[0] * (u[4] * u[8] - u[5] * u[7]) - u[1] * (u[3] * u[8] - u[5] * u[6]) +
+                      u[2] * (u[3] * u[7] - u[4] * u[6]);
+    dev = fmax(dev, fmax(fabs(det.re - 1.0), fabs(det.im)));
+    if (!(dev <= tol)) atomicOr(bad, 1);
+}
+
+// The first two rows of every link: 24 planes per site, plane mu*6 + 3*row + col
+// (an SU(3) link's third row is the conjugated cross product of the two)
+template <typename S>
+__global__ void k_links12_convert(Geom g, const double2 *src, typename S::T2 *dst)
+{
+    int gi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi >= g.V) return;
+    int d, s;
+    split_index(g, gi, d, s);
+    for (int mu = 0; mu < 4; mu++)
+        for (int k = 0; k < 6; k++) {
+            double2 a = __ldg(src + ((int64_t)d * 36 + mu * 9 + k) * g.Vd + s);
+            st_c<double>(dst + ((int64_t)d * 24 + mu * 6 + k) * g.Vd + s, mk(a.x, a.y));
+        }
+}
+
 // clover blocks: 36 planes per site; 16-bit formats get one scale per site
 template <typename S>
 __global__ void k_clover_convert(Geom g, const double2 *src, Field<S> dst)
@@ -381,6 +424,27 @@ qdd_status launch_links_convert(Gauge *g, qdd_prec dp, void *dst, cudaStream_t s
     QDD_DISPATCH_PREC(dp, S, {
         k_links_convert<S><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, g->links64.as<double2>(),
                                                                         (typename S::T2 *)dst);
+    });
+    QDD_CUDA(cudaGetLastError());
+    return QDD_OK;
+}
+
+qdd_status launch_su3_check(Gauge *g, double tol, int *d_bad, cudaStream_t s)
+{
+    const int64_t n = (int64_t)g->hg.V * 4;
+    LaunchScope ls(g->ctx->timer, K_OTHER, s);
+    QDD_CUDA(cudaMemsetAsync(d_bad, 0, sizeof(int), s));
+    k_su3_check<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g->geom, g->links64.as<double2>(), tol, d_bad);
+    QDD_CUDA(cudaGetLastError());
+    return QDD_OK;
+}
+
+qdd_status launch_links12_convert(Gauge *g, qdd_prec dp, void *dst, cudaStream_t s)
+{
+    LaunchScope ls(g->ctx->timer, K_OTHER, s);
+    QDD_DISPATCH_PREC(dp, S, {
+        k_links12_convert<S><<<grid_sites(g->hg.V, 1, 256), 256, 0, s>>>(g->geom, g->links64.as<double2>(),
+                                                                          (typename S::T2 *)dst);
     });
     QDD_CUDA(cudaGetLastError());
     return QDD_OK;

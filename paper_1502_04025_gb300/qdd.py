@@ -76,6 +76,8 @@ _SIGS = {
     "qdd_memory": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
     "qdd_create_gauge_field": (ctypes.c_int, [_vp, _ip, _ip, _vp, ctypes.c_int, ctypes.POINTER(_vp)]),
     "qdd_destroy_gauge": (None, [_vp]),
+    "qdd_set_link_compression": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "qdd_link_compression": (ctypes.c_int, [_vp, _ip, _ip]),
     "qdd_set_clover": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double]),
     "qdd_get_clover": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
     "qdd_apply_D": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp]),
@@ -212,6 +214,18 @@ def qdd_create_gauge_field(ctx, L, dom, links):
 
 def qdd_destroy_gauge(g):
     _lib.qdd_destroy_gauge(g)
+
+
+def qdd_set_link_compression(g, two_rows: bool):
+    _check(_lib.qdd_set_link_compression(g, int(bool(two_rows))), "qdd_set_link_compression")
+
+
+def qdd_link_compression(g):
+    """(two_rows, is_su3): whether the FP32/16-bit operator reads two rows
+    per link, and whether every link passed the SU(3) check."""
+    t, u = ctypes.c_int(), ctypes.c_int()
+    _check(_lib.qdd_link_compression(g, ctypes.byref(t), ctypes.byref(u)), "qdd_link_compression")
+    return bool(t.value), bool(u.value)
 
 
 def qdd_set_clover(g, c_sw: float, kappa: float):
