@@ -559,7 +559,11 @@ def run_op_bench(args):
            "peak_kind": "of measured" if pk_kind == "measured" else "of fallback"}
     two_rows, _ = qdd.qdd_link_compression(g)
     out["link_rows"] = 2 if two_rows else 3
-    for prec in args.op_precs.split(","):
+    for name in args.op_precs.split(","):
+        # "<prec>_three_rows": the same operator reading whole links
+        prec = name.split("_")[0]
+        rows3 = name.endswith("_three_rows") or not two_rows
+        qdd.qdd_set_link_compression(g, not rows3)
         for _ in range(3):
             qdd.qdd_apply_D(g, xs, prec, out=ys)
         qdd.qdd_set_profiling(ctx, qdd.QDD_PROF_DSLASH)
@@ -569,8 +573,8 @@ def run_op_bench(args):
         kd = qdd.qdd_get_kernel_times(ctx, reset=True)
         qdd.qdd_set_profiling(ctx, 0)
         ms = kd["dslash"][0] / kd["dslash"][1]
-        bps = op_bytes_per_site(prec, not two_rows)
-        out[prec] = {"ms": ms, "gflops": 1848 * Vl / (ms * 1e-3) / 1e9, "gbs": bps * Vl / (ms * 1e-3) / 1e9,
+        bps = op_bytes_per_site(prec, rows3)
+        out[name] = {"ms": ms, "gflops": 1848 * Vl / (ms * 1e-3) / 1e9, "gbs": bps * Vl / (ms * 1e-3) / 1e9,
                      "frac_hbm": bps * Vl / (ms * 1e-3) / 1e9 / pk["hbm_gbs"], "bytes_per_site": bps}
     print(json.dumps(out), flush=True)
     qdd.qdd_destroy_gauge(g)
