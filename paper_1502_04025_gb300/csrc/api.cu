@@ -641,7 +641,7 @@ qdd_status qdd_cdot_multi(qdd_ctx *ctx, const double *v, int nvec, int64_t ld, c
     QDD_CUDA(cudaSetDevice(ctx->device));
     cudaStream_t s = (cudaStream_t)stream;
     std::lock_guard<std::mutex> lk(ctx->red_mu);
-    QDD_TRY(ctx->red_scratch.ensure(ctx, blas_scratch_elems(ctx) * sizeof(double2)));
+    QDD_TRY(blas_scratch_ensure(ctx, ctx->red_scratch));
     QDD_TRY(blas_cdot_multi(ctx, (const double2 *)v, nvec, ld, (const double2 *)w, n, (double2 *)out,
                             ctx->red_scratch.as<double2>(), s));
     QDD_CUDA(cudaStreamSynchronize(s));

@@ -26,7 +26,24 @@ int blas_blocks(const Ctx *ctx, int64_t n)
     return (int)(want < 1 ? 1 : want);
 }
 
-size_t blas_scratch_elems(const Ctx *ctx) { return (size_t)2 * (ctx->nsm > 0 ? ctx->nsm : 148) * kNV; }
+// per-block partials of up to 2 blocks per SM, then one slot whose first
+// word counts the blocks that have finished (zero between launches)
+size_t blas_scratch_elems(const Ctx *ctx) { return (size_t)2 * (ctx->nsm > 0 ? ctx->nsm : 148) * kNV + 1; }
+
+static unsigned *scratch_counter(const Ctx *ctx, double2 *scratch)
+{
+    return (unsigned *)(scratch + blas_scratch_elems(ctx) - 1);
+}
+
+qdd_status blas_scratch_ensure(Ctx *ctx, DevMem &m)
+{
+    const size_t bytes = blas_scratch_elems(ctx) * sizeof(double2);
+    if (m.p && m.bytes >= bytes) return QDD_OK;
+    QDD_TRY(m.alloc(ctx, bytes));
+    QDD_CUDA(cudaMemset(scratch_counter(ctx, m.as<double2>()), 0, sizeof(unsigned)));
+    QDD_CUDA(cudaDeviceSynchronize());
+    return QDD_OK;
+}
 
 __device__ __forceinline__ double2 dsum2(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 
@@ -47,9 +64,42 @@ __device__ __forceinline__ void block_reduce(double2 *acc, double2 *sm /* [kBT/3
     __syncthreads();
 }
 
+// The last block to finish sums every block's partials (stride `stride`,
+// nv values each) in block order, with the same arithmetic as
+// k_reduce_final, writes out[0..nv) and resets the counter.  Called by all
+// threads after the block's own partials are written.
+template <int NV>
+__device__ __forceinline__ void last_block_final(const double2 *part, int stride, int nv, unsigned *count,
+                                                 double2 *out, double2 *sm /* [kBT/32][NV] */)
+{
+    __shared__ bool last;
+    __threadfence();  // this block's partials before its count
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(count, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double2 acc[NV];
+#pragma unroll
+    for (int j = 0; j < NV; j++) acc[j] = make_double2(0, 0);
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += kBT)
+#pragma unroll
+        for (int j = 0; j < NV; j++)
+            if (j < nv) acc[j] = dsum2(acc[j], __ldcg(part + (int64_t)b * stride + j));
+    block_reduce<NV>(acc, sm);
+    if (threadIdx.x < nv) {
+        double2 t = make_double2(0, 0);
+        for (int ww = 0; ww < kBT / 32; ww++) t = dsum2(t, sm[ww * NV + threadIdx.x]);
+        out[threadIdx.x] = t;
+    }
+    if (threadIdx.x == 0) *count = 0;
+}
+
+// count != NULL: the last block also writes the final sums to out
 template <int NV>
 __global__ void __launch_bounds__(kBT) k_cdot_partial(const double2 *__restrict__ v, int nvec, int64_t ld,
-                                                      const double2 *__restrict__ w, int64_t n, double2 *part)
+                                                      const double2 *__restrict__ w, int64_t n, double2 *part,
+                                                      unsigned *count = nullptr, double2 *out = nullptr)
 {
     __shared__ double2 sm[(kBT / 32) * NV];
     double2 acc[NV];
@@ -72,6 +122,10 @@ __global__ void __launch_bounds__(kBT) k_cdot_partial(const double2 *__restrict_
         double2 s = make_double2(0, 0);
         for (int ww = 0; ww < kBT / 32; ww++) s = dsum2(s, sm[ww * NV + threadIdx.x]);
         part[(int64_t)blockIdx.x * kNV + threadIdx.x] = s;
+    }
+    if (count) {
+        __syncthreads();  // sm is reused
+        last_block_final<NV>(part, kNV, nvec, count, out, sm);
     }
 }
 
@@ -96,7 +150,7 @@ __global__ void __launch_bounds__(kBT) k_reduce_final(const double2 *part, int n
 template <int NV>
 __global__ void __launch_bounds__(kBT) k_caxpy_norm(const double2 *__restrict__ v, int nvec, int64_t ld,
                                                     const double2 *__restrict__ coef, double2 *w, int64_t n,
-                                                    double2 *part)
+                                                    double2 *part, unsigned *count, double2 *norm2_out)
 {
     __shared__ double2 sm[kBT / 32];
     double2 c[NV];
@@ -126,14 +180,23 @@ __global__ void __launch_bounds__(kBT) k_caxpy_norm(const double2 *__restrict__ 
             for (int ww = 0; ww < kBT / 32; ww++) t = dsum2(t, sm[ww]);
             part[blockIdx.x] = t;
         }
+        __syncthreads();  // sm is reused
+        last_block_final<1>(part, 1, 1, count, norm2_out, sm);
     }
 }
 
 // out = w / sqrt(norm2[0]) (out may alias w)
 __global__ void k_scale_by_norm(const double2 *w, int64_t n, const double2 *norm2, double2 *out)
 {
-    double nn = norm2[0].x;
-    double f = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
+    // once per block: FP64 square root and division are long sequences on
+    // the FP64 pipe
+    __shared__ double fs;
+    if (threadIdx.x == 0) {
+        double nn = norm2[0].x;
+        fs = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
+    }
+    __syncthreads();
+    const double f = fs;
     for (int64_t k = (int64_t)blockIdx.x * kBT + threadIdx.x; k < n; k += (int64_t)gridDim.x * kBT) {
         double2 a = w[k];
         out[k] = make_double2(a.x * f, a.y * f);
@@ -225,16 +288,11 @@ qdd_status blas_cdot_multi(Ctx *ctx, const double2 *v, int nvec, int64_t ld, con
     const int nb = blas_blocks(ctx, n);
     for (int j0 = 0; j0 < nvec; j0 += kNV) {
         int nv = nvec - j0 < kNV ? nvec - j0 : kNV;
-        {
-            LaunchScope ls(ctx->timer, K_BLAS, s);
-            nv_dispatch(nv, [&](auto c) {
-                k_cdot_partial<decltype(c)::value><<<nb, kBT, 0, s>>>(v + j0 * ld, nv, ld, w, n, scratch);
-            });
-        }
-        {
-            LaunchScope ls(ctx->timer, K_BLAS, s);
-            k_reduce_final<<<nv, kBT, 0, s>>>(scratch, nb, kNV, out + j0, 0);
-        }
+        LaunchScope ls(ctx->timer, K_BLAS, s);
+        nv_dispatch(nv, [&](auto c) {
+            k_cdot_partial<decltype(c)::value><<<nb, kBT, 0, s>>>(v + j0 * ld, nv, ld, w, n, scratch,
+                                                                  scratch_counter(ctx, scratch), out + j0);
+        });
     }
     QDD_CUDA(cudaGetLastError());
     return QDD_OK;
@@ -251,19 +309,17 @@ qdd_status blas_caxpy_multi_norm(Ctx *ctx, const double2 *v, int nvec, int64_t l
         {
             LaunchScope ls(ctx->timer, K_BLAS, s);
             double2 *part = (last && norm2_out) ? scratch : nullptr;
+            unsigned *cnt = scratch_counter(ctx, scratch);
             if (nv == 0)
-                k_caxpy_norm<1><<<nb, kBT, 0, s>>>(v, 0, ld, coef, w, n, part);
+                k_caxpy_norm<1><<<nb, kBT, 0, s>>>(v, 0, ld, coef, w, n, part, cnt, norm2_out);
             else
                 nv_dispatch(nv, [&](auto c) {
-                    k_caxpy_norm<decltype(c)::value><<<nb, kBT, 0, s>>>(v + j0 * ld, nv, ld, coef + j0, w, n, part);
+                    k_caxpy_norm<decltype(c)::value><<<nb, kBT, 0, s>>>(v + j0 * ld, nv, ld, coef + j0, w, n, part,
+                                                                        cnt, norm2_out);
                 });
         }
         j0 += nv;
     } while (j0 < nvec);
-    if (norm2_out) {
-        LaunchScope ls(ctx->timer, K_BLAS, s);
-        k_reduce_final<<<1, kBT, 0, s>>>(scratch, nb, 1, norm2_out, 0);
-    }
     QDD_CUDA(cudaGetLastError());
     return QDD_OK;
 }
@@ -276,8 +332,11 @@ qdd_status blas_norm2(Ctx *ctx, const double2 *w, int64_t n, double2 *out, doubl
 qdd_status blas_scale_by_norm(Ctx *ctx, const double2 *w, int64_t n, const double2 *norm2, double2 *out,
                               cudaStream_t s)
 {
+    // one element per thread: a memory-bound pass needs every load in flight
+    // at once (the reduction kernels' two blocks per SM keep too few)
+    const int64_t nb = (n + kBT - 1) / kBT;
     LaunchScope ls(ctx->timer, K_BLAS, s);
-    k_scale_by_norm<<<blas_blocks(ctx, n), kBT, 0, s>>>(w, n, norm2, out);
+    k_scale_by_norm<<<(unsigned)(nb < (1LL << 30) ? nb : (1LL << 30)), kBT, 0, s>>>(w, n, norm2, out);
     QDD_CUDA(cudaGetLastError());
     return QDD_OK;
 }

@@ -273,6 +273,8 @@ size_t sap_smem_bytes(const HostGeom &hg, qdd_prec prec, bool stage_links, bool 
 // blas_scratch_elems(ctx) double2 of per-block partial sums)
 int blas_blocks(const Ctx *ctx, int64_t n);
 size_t blas_scratch_elems(const Ctx *ctx);
+// allocates a reduction scratch buffer (if too small) with its block counter at zero
+qdd_status blas_scratch_ensure(Ctx *ctx, DevMem &m);
 qdd_status blas_cdot_multi(Ctx *ctx, const double2 *v, int nvec, int64_t ld, const double2 *w, int64_t n,
                            double2 *out, double2 *scratch, cudaStream_t s);
 qdd_status blas_caxpy_multi_norm(Ctx *ctx, const double2 *v, int nvec, int64_t ld, const double2 *coef, double2 *w,

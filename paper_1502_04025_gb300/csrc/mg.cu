@@ -761,7 +761,7 @@ qdd_status qdd_mg_setup(qdd_gauge *g, const qdd_mg_params *p, const double *w0, 
     QDD_TRY(M->cb.alloc(ctx, M->ncoarse * sizeof(float2)));
     QDD_TRY(M->cst.alloc(ctx, sizeof(CgState)));
     DevMem dscr, ddev;  // setup normalisation
-    QDD_TRY(dscr.alloc(ctx, blas_scratch_elems(ctx) * sizeof(double2)));
+    QDD_TRY(blas_scratch_ensure(ctx, dscr));
     QDD_TRY(ddev.alloc(ctx, sizeof(double2)));
     QDD_TRY(ensure_copy(g, QDD_PREC_F32, s));
     if (zp == QDD_PREC_F32 || sp != QDD_PREC_F64) QDD_TRY(ensure_copy(g, sp, s));

@@ -109,7 +109,7 @@ static qdd_status ensure_ws(Gauge *g, Workspace &w, int m, int B, qdd_prec sp, b
     }
     ScalarMap sm{m, B};
     QDD_TRY(w.dev.ensure(c, sm.total() * sizeof(double2)));
-    QDD_TRY(w.scratch.ensure(c, blas_scratch_elems(c) * sizeof(double2)));
+    QDD_TRY(blas_scratch_ensure(c, w.scratch));
     QDD_TRY(w.err.ensure(c, sizeof(int)));
     if (w.host_elems < sm.total()) {
         if (w.host) cudaFreeHost(w.host);
