@@ -185,8 +185,9 @@ __global__ void __launch_bounds__(kBT) k_caxpy_norm(const double2 *__restrict__ 
     }
 }
 
-// out = w / sqrt(norm2[0]) (out may alias w)
-__global__ void k_scale_by_norm(const double2 *w, int64_t n, const double2 *norm2, double2 *out)
+// out = w / sqrt(norm2[0]) (out may alias w); out32 (optional) gets the same
+// vector rounded to FP32
+__global__ void k_scale_by_norm(const double2 *w, int64_t n, const double2 *norm2, double2 *out, float2 *out32)
 {
     // once per block: FP64 square root and division are long sequences on
     // the FP64 pipe
@@ -199,7 +200,9 @@ __global__ void k_scale_by_norm(const double2 *w, int64_t n, const double2 *norm
     const double f = fs;
     for (int64_t k = (int64_t)blockIdx.x * kBT + threadIdx.x; k < n; k += (int64_t)gridDim.x * kBT) {
         double2 a = w[k];
-        out[k] = make_double2(a.x * f, a.y * f);
+        a = make_double2(a.x * f, a.y * f);
+        out[k] = a;
+        if (out32) out32[k] = make_float2((float)a.x, (float)a.y);
     }
 }
 
@@ -330,13 +333,13 @@ qdd_status blas_norm2(Ctx *ctx, const double2 *w, int64_t n, double2 *out, doubl
 }
 
 qdd_status blas_scale_by_norm(Ctx *ctx, const double2 *w, int64_t n, const double2 *norm2, double2 *out,
-                              cudaStream_t s)
+                              cudaStream_t s, float2 *out32)
 {
     // one element per thread: a memory-bound pass needs every load in flight
     // at once (the reduction kernels' two blocks per SM keep too few)
     const int64_t nb = (n + kBT - 1) / kBT;
     LaunchScope ls(ctx->timer, K_BLAS, s);
-    k_scale_by_norm<<<(unsigned)(nb < (1LL << 30) ? nb : (1LL << 30)), kBT, 0, s>>>(w, n, norm2, out);
+    k_scale_by_norm<<<(unsigned)(nb < (1LL << 30) ? nb : (1LL << 30)), kBT, 0, s>>>(w, n, norm2, out, out32);
     QDD_CUDA(cudaGetLastError());
     return QDD_OK;
 }

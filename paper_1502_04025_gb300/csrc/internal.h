@@ -280,8 +280,10 @@ qdd_status blas_cdot_multi(Ctx *ctx, const double2 *v, int nvec, int64_t ld, con
 qdd_status blas_caxpy_multi_norm(Ctx *ctx, const double2 *v, int nvec, int64_t ld, const double2 *coef, double2 *w,
                                  int64_t n, double2 *norm2_out, double2 *scratch, cudaStream_t s);
 qdd_status blas_norm2(Ctx *ctx, const double2 *w, int64_t n, double2 *out, double2 *scratch, cudaStream_t s);
+// out = w / |w| from the squared norm on the device; out32 (optional) also gets
+// the result rounded to FP32
 qdd_status blas_scale_by_norm(Ctx *ctx, const double2 *w, int64_t n, const double2 *norm2, double2 *out,
-                              cudaStream_t s);
+                              cudaStream_t s, float2 *out32 = nullptr);
 qdd_status blas_axpy_multi(Ctx *ctx, const void *z, bool z_f32, int nvec, int64_t ld, const double2 *coef,
                            double2 *x, int64_t n, cudaStream_t s);
 // out_c (+)= sum_i src_i P[i*ldp + c], c < ncols (P on the device, row-major)

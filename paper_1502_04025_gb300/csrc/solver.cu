@@ -202,6 +202,10 @@ qdd_status solve_impl(Gauge *g, Workspace *wsp, const double *b_in, double *x_ou
     std::vector<int> kr(B, 0);
     int j0 = 0;                  // columns carried over by a deflated restart (same for all rhs)
     bool pending_dr = false;     // the previous cycle ended ready for a deflated restart
+    // FP32 Schwarz input: written by the scaling that makes v_j, which saves a
+    // conversion pass per step (rho_ready: rho holds v_j of every right-hand side)
+    float2 *rho32 = (p->use_sap == 1 && spinor_store(sp) == QDD_PREC_F32) ? w.rho.as<float2>() : nullptr;
+    bool rho_ready = false;
     const int kdr = p->dr_k;
     w.hist.clear();
     int iters = 0, restarts = 0, deflated = 0;
@@ -241,6 +245,7 @@ qdd_status solve_impl(Gauge *g, Workspace *wsp, const double *b_in, double *x_ou
         if (cycle > p->max_restarts) break;
 
         // ---- deflated restart (harmonic Ritz vectors of the last cycle), else plain restart
+        rho_ready = false;
         bool deflate = pending_dr;
         std::vector<dense::Mat> Pm(B);
         if (deflate) {
@@ -349,7 +354,9 @@ qdd_status solve_impl(Gauge *g, Workspace *wsp, const double *b_in, double *x_ou
             deflated++;
         } else {
             for (int r = 0; r < B; r++)
-                QDD_TRY(blas_scale_by_norm(ctx, R0 + r * n, n, dev + sm.nrm1() + r, V + r * n, s));
+                QDD_TRY(blas_scale_by_norm(ctx, R0 + r * n, n, dev + sm.nrm1() + r, V + r * n, s,
+                                           rho32 ? rho32 + r * n : nullptr));
+            rho_ready = rho32 != nullptr;
             for (int r = 0; r < B; r++) {
                 H[r] = dense::Mat(m + 1, m);
                 cv[r].assign(m + 1, zc(0, 0));
@@ -370,8 +377,10 @@ qdd_status solve_impl(Gauge *g, Workspace *wsp, const double *b_in, double *x_ou
             if (p->use_sap == 2) {
                 QDD_TRY(mg_vcycle(g, vj, zj, zp, s));
             } else if (p->use_sap) {
-                QDD_TRY(launch_spinor_convert(g, vj, nullptr, QDD_PREC_F64, w.rho.p, w.rho_s.as<float>(),
-                                              spinor_store(sp), B, s));
+                if (!rho_ready)
+                    QDD_TRY(launch_spinor_convert(g, vj, nullptr, QDD_PREC_F64, w.rho.p, w.rho_s.as<float>(),
+                                                  spinor_store(sp), B, s));
+                rho_ready = false;
                 sb.psi = zj;
                 SeqScope seq(ctx->timer, K_SAP, s);
                 for (int hs = 0; hs < 2 * p->ncy; hs++)
@@ -439,8 +448,10 @@ qdd_status solve_impl(Gauge *g, Workspace *wsp, const double *b_in, double *x_ou
             }
             iters++;
             bool all_done = true;
+            int scaled = 0;
             for (int r = 0; r < B; r++) {
                 if (!open[r]) continue;
+                scaled++;
                 dense::Mat &h = H[r];
                 for (int i = 0; i <= j; i++) {
                     double2 a = host[sm.dots1() + (size_t)r * (m + 2) + i];
@@ -458,9 +469,10 @@ qdd_status solve_impl(Gauge *g, Workspace *wsp, const double *b_in, double *x_ou
                     status = QDD_ENAN;
                 }
                 h(j + 1, j) = hn;
-                // v_{j+1} = w / h_{j+1,j}
+                // v_{j+1} = w / h_{j+1,j}, with its FP32 copy for the next
+                // preconditioner when every right-hand side goes on
                 QDD_TRY(blas_scale_by_norm(ctx, wv + r * n, n, dev + (two[r] ? sm.nrm2() : sm.nrm1()) + r, wv + r * n,
-                                           s));
+                                           s, rho32 ? rho32 + r * n : nullptr));
                 // residual estimate: min |c - Hbar y| over the j+1 columns
                 dense::Mat Hs(j + 2, j + 1);
                 for (int i = 0; i < j + 2; i++)
@@ -473,6 +485,7 @@ qdd_status solve_impl(Gauge *g, Workspace *wsp, const double *b_in, double *x_ou
                 if (est[r] <= p->tol || hn == 0.0) open[r] = 0;
                 all_done = all_done && !open[r];
             }
+            rho_ready = rho32 != nullptr && scaled == B;
             if (status != QDD_OK || all_done) break;
         }
         if (status != QDD_OK) break;
