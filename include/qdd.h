@@ -262,6 +262,10 @@ qdd_status qdd_solve(qdd_gauge *g, const double *b, double *x, int on_device, co
  *               zero (fewer on an exact breakdown), run on the device without
  *               host round trips, z = P e, then z += M_SAP(v - D z) with
  *               post_ncy Schwarz cycles
+ *   bootstrap   the adaptive part of the setup, repeated `bootstrap` times:
+ *               each w_k becomes the V-cycle of the method built so far
+ *               applied to column k of P (as a fine field), normalised, and
+ *               P and D_c are rebuilt from the new w_k
  */
 typedef struct {
     int nv;            /* vectors per aggregate and chirality (1..16) */
@@ -271,10 +275,11 @@ typedef struct {
     int post_ncy;      /* Schwarz cycles after the coarse correction (0 = none) */
     int coarse_iters;  /* steps of the coarse GMRES cycle (1..64) */
     qdd_prec sap_prec; /* the smoother's precision (as qdd_solve_params) */
+    int bootstrap;     /* adaptive setup passes after the first build (0..8) */
 } qdd_mg_params;
 
 /* nv 8, setup_iters 3, setup_ncy 2, nmr 4, post_ncy 2, coarse_iters 12,
- * FP32 smoother. */
+ * FP32 smoother, no bootstrap pass. */
 void qdd_mg_default_params(qdd_mg_params *p);
 
 /* Builds the preconditioner on g (replacing an earlier one).  w0: nv random

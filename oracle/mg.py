@@ -21,6 +21,10 @@ the library, listed in the design notes):
   V-cycle      e_c ~ D_c^{-1} P^H v by one GMRES cycle of `coarse_iters` steps
                from zero (or, for the pins, an exact solve), z = P e_c,
                r = v - D z, z += M_SAP(r) (`post_ncy` Schwarz cycles)
+  bootstrap    the adaptive setup, `bootstrap` times: w_k = the V-cycle of the
+               method built so far applied to the k-th prolongator column
+               (column k of every block, as one fine field), normalised; P and
+               D_c rebuilt from the new w_k
 """
 from __future__ import annotations
 
@@ -45,7 +49,7 @@ def aggregates(L, dom):
 
 class TwoLevel:
     def __init__(self, L, dom, U, A, Ainv, kappa, w0, setup_iters=2, setup_ncy=2, nmr=4, post_ncy=2,
-                 coarse_iters=24):
+                 coarse_iters=24, bootstrap=0):
         self.L, self.dom, self.U, self.A, self.Ainv, self.kappa = tuple(L), tuple(dom), U, A, Ainv, kappa
         self.nmr, self.post_ncy, self.coarse_iters = nmr, post_ncy, coarse_iters
         self.V = int(np.prod(L))
@@ -58,9 +62,20 @@ class TwoLevel:
                 w[k] = self.sap(w[k], setup_ncy)
                 w[k] /= np.linalg.norm(w[k])
         self.w_smoothed = w.copy()
-        # prolongator: per aggregate and chirality, MGS twice over the nv vectors;
-        # block (a, chi) is a (6 * sites, nv) matrix with orthonormal columns
         self.sites = [np.nonzero(self.agg == a)[0] for a in range(self.nagg)]
+        self.nc = self.nagg * 2 * self.nv
+        self.build(w)
+        for _ in range(bootstrap):
+            cols = self.basis()
+            w = np.array([self.vcycle(cols[k]) for k in range(self.nv)])
+            for k in range(self.nv):
+                w[k] /= np.linalg.norm(w[k])
+            self.build(w)
+
+    def build(self, w):
+        """Prolongator from the test vectors w (nv, V, 4, 3): per aggregate and
+        chirality, MGS twice over the nv vectors, so block (a, chi) is a
+        (6 * sites, nv) matrix with orthonormal columns; then D_c."""
         self.Pb = {}
         for a in range(self.nagg):
             s = self.sites[a]
@@ -72,7 +87,6 @@ class TwoLevel:
                             blk[k] -= np.vdot(blk[l], blk[k]) * blk[l]
                         blk[k] /= np.linalg.norm(blk[k])
                 self.Pb[a, chi] = blk.T.copy()
-        self.nc = self.nagg * 2 * self.nv
         self.Dc = self.coarse_matrix()
 
     def basis(self):

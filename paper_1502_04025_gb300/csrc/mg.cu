@@ -652,10 +652,10 @@ static qdd_status mg_coarse_solve(Gauge *g, Multigrid &M, cudaStream_t s)
     return QDD_OK;
 }
 
-// z = M_MG v for one right-hand side: v FP64 (domain layout), z in zp storage.
-qdd_status mg_vcycle(Gauge *g, const double2 *v, void *z, qdd_prec zp, cudaStream_t s)
+// z = M_MG v for one right-hand side: v FP64 (domain layout, not M's own
+// buffers), z in zp storage.
+static qdd_status mg_vcycle_with(Gauge *g, Multigrid &M, const double2 *v, void *z, qdd_prec zp, cudaStream_t s)
 {
-    Multigrid &M = *g->mg;
     const int64_t nfine = (int64_t)g->hg.V * 12;
     const int64_t stride = nfine;
     {
@@ -690,12 +690,41 @@ qdd_status mg_vcycle(Gauge *g, const double2 *v, void *z, qdd_prec zp, cudaStrea
     return QDD_OK;
 }
 
+qdd_status mg_vcycle(Gauge *g, const double2 *v, void *z, qdd_prec zp, cudaStream_t s)
+{
+    return mg_vcycle_with(g, *g->mg, v, z, zp, s);
+}
+
+// The prolongator and coarse operator from test vectors w64 (nv FP64 fields,
+// overwritten): per aggregate and chirality the vectors are orthonormalised,
+// P takes them in FP32, and D_c = P^H D P is rebuilt.  The captured coarse
+// cycle reads D_c in place, so it stays valid.
+static qdd_status mg_build(Gauge *g, Multigrid &M, double2 *w64, cudaStream_t s)
+{
+    const HostGeom &hg = g->hg;
+    const int64_t nfine = (int64_t)hg.V * 12;
+    k_mg_orth<<<hg.Nd * 2, kMgThreads, 0, s>>>(w64, M.nv, nfine, hg.Vd);
+    QDD_CUDA(cudaGetLastError());
+    QDD_TRY(launch_spinor_convert(g, w64, nullptr, QDD_PREC_F64, M.P.p, nullptr, QDD_PREC_F32, M.nv, s));
+    PrecCopy &c = g->copies[QDD_PREC_F32];
+    MgBasis B{M.P.as<float2>(), nfine, hg.Vd, M.nv};
+    const int bthreads = (hg.Vh + 31) / 32 * 32;
+    const size_t smem = (size_t)(bthreads / 32) * 9 * M.nc * sizeof(float2);
+    QDD_CUDA(cudaFuncSetAttribute(k_mg_coarse_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_mg_coarse_build<<<hg.Nd, bthreads, smem, s>>>(g->geom, Field<StF32>{c.links.as<float2>(), nullptr},
+                                                  Field<StF32>{c.clov.as<float2>(), nullptr}, B, (float)g->kappa,
+                                                  M.Y.as<float2>());
+    QDD_CUDA(cudaGetLastError());
+    return QDD_OK;
+}
+
 qdd_prec mg_smoother_prec(const Gauge *g) { return g->mg ? g->mg->p.sap_prec : QDD_PREC_F32; }
 
 static qdd_status mg_check(const qdd_mg_params *p)
 {
     if (!p || p->nv < 1 || p->nv > 16 || p->setup_iters < 0 || p->setup_ncy < 1 || p->nmr < 0 || p->post_ncy < 0 ||
-        p->coarse_iters < 1 || p->coarse_iters > kCgMaxM || !is_sap_prec(p->sap_prec)) {
+        p->coarse_iters < 1 || p->coarse_iters > kCgMaxM || !is_sap_prec(p->sap_prec) || p->bootstrap < 0 ||
+        p->bootstrap > 8) {
         set_error("invalid multigrid parameters");
         return QDD_EINVAL;
     }
@@ -788,19 +817,27 @@ qdd_status qdd_mg_setup(qdd_gauge *g, const qdd_mg_params *p, const double *w0, 
             QDD_TRY(blas_norm2(ctx, wk, nfine, dev, scr, s));
             QDD_TRY(blas_scale_by_norm(ctx, wk, nfine, dev, wk, s));
         }
-    k_mg_orth<<<hg.Nd * 2, kMgThreads, 0, s>>>(w64.as<double2>(), nv, nfine, hg.Vd);
-    QDD_CUDA(cudaGetLastError());
-    QDD_TRY(launch_spinor_convert(g, w64.p, nullptr, QDD_PREC_F64, M->P.p, nullptr, QDD_PREC_F32, nv, s));
-    // coarse operator
-    PrecCopy &c = g->copies[QDD_PREC_F32];
-    MgBasis B{M->P.as<float2>(), nfine, hg.Vd, nv};
-    const int bthreads = (hg.Vh + 31) / 32 * 32;
-    const size_t smem = (size_t)(bthreads / 32) * 9 * M->nc * sizeof(float2);
-    QDD_CUDA(cudaFuncSetAttribute(k_mg_coarse_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_mg_coarse_build<<<hg.Nd, bthreads, smem, s>>>(g->geom, Field<StF32>{c.links.as<float2>(), nullptr},
-                                                  Field<StF32>{c.clov.as<float2>(), nullptr}, B, (float)g->kappa,
-                                                  M->Y.as<float2>());
-    QDD_CUDA(cudaGetLastError());
+    QDD_TRY(mg_build(g, *M, w64.as<double2>(), s));
+    QDD_TRY(mg_capture(g, *M));
+    // bootstrap (the adaptive setup): each test vector becomes the V-cycle of
+    // the two-level method just built applied to its prolongator column,
+    // normalised; P and D_c are rebuilt from them
+    if (p->bootstrap > 0) {
+        DevMem vin;
+        QDD_TRY(vin.alloc(ctx, nfine * sizeof(double2)));
+        for (int b = 0; b < p->bootstrap; b++) {
+            for (int k = 0; k < nv; k++) {
+                double2 *wk = w64.as<double2>() + k * nfine;
+                QDD_TRY(launch_spinor_convert(g, M->P.as<float2>() + k * nfine, nullptr, QDD_PREC_F32, vin.p,
+                                              nullptr, QDD_PREC_F64, 1, s));
+                QDD_TRY(mg_vcycle_with(g, *M, vin.as<double2>(), zt.p, zp, s));
+                QDD_TRY(launch_spinor_convert(g, zt.p, nullptr, zp, wk, nullptr, QDD_PREC_F64, 1, s));
+                QDD_TRY(blas_norm2(ctx, wk, nfine, dev, scr, s));
+                QDD_TRY(blas_scale_by_norm(ctx, wk, nfine, dev, wk, s));
+            }
+            QDD_TRY(mg_build(g, *M, w64.as<double2>(), s));
+        }
+    }
     QDD_CUDA(cudaStreamSynchronize(s));
     int herr = 0;
     QDD_CUDA(cudaMemcpy(&herr, M->err.p, sizeof(int), cudaMemcpyDeviceToHost));
@@ -808,7 +845,6 @@ qdd_status qdd_mg_setup(qdd_gauge *g, const qdd_mg_params *p, const double *w0, 
         set_error("Schwarz smoother error flag %d during the multigrid setup", herr);
         return QDD_ECUDA;
     }
-    QDD_TRY(mg_capture(g, *M));
     g->mg = M;
     return QDD_OK;
 }

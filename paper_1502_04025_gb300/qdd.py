@@ -53,7 +53,7 @@ class qdd_report(ctypes.Structure):
 class qdd_mg_params(ctypes.Structure):
     _fields_ = [("nv", ctypes.c_int), ("setup_iters", ctypes.c_int), ("setup_ncy", ctypes.c_int),
                 ("nmr", ctypes.c_int), ("post_ncy", ctypes.c_int), ("coarse_iters", ctypes.c_int),
-                ("sap_prec", ctypes.c_int)]
+                ("sap_prec", ctypes.c_int), ("bootstrap", ctypes.c_int)]
 
 
 class qdd_tune_result(ctypes.Structure):
@@ -378,6 +378,8 @@ def qdd_mg_default_params(**kw) -> qdd_mg_params:
     p = qdd_mg_params()
     _lib.qdd_mg_default_params(ctypes.byref(p))
     for k, v in kw.items():
+        if k not in dict(qdd_mg_params._fields_):
+            raise TypeError(f"unknown multigrid parameter {k!r}")
         setattr(p, k, _prec(v) if k == "sap_prec" else v)
     return p
 

@@ -62,6 +62,26 @@ def test_basis_and_coarse_correction_match_reference(q, ctx, ora, L, dom):
     q.qdd_destroy_gauge(g)
 
 
+def test_bootstrap_matches_reference(q, ctx, ora):
+    """The adaptive setup pass: each test vector replaced by the V-cycle of
+    the first build applied to its prolongator column, P and D_c rebuilt."""
+    from oracle import mg
+    U, A, Ainv, g = _problem(q, ctx, ora, L44, DOM2, 0.13)
+    nv = 4
+    w0 = inputs.gaussian_source(L44, 4001, nrhs=nv)
+    kw = dict(setup_iters=2, setup_ncy=2, nmr=4, post_ncy=2, coarse_iters=16, bootstrap=1)
+    ref = mg.TwoLevel(L44, DOM2, U, A, Ainv, 0.13, w0, **kw)
+    q.qdd_mg_setup(g, np.ascontiguousarray(w0), nv=nv, sap_prec="f64", **kw)
+    V = int(np.prod(L44))
+    # FP32 coarse cycle inside the bootstrap V-cycles, FP32 storage of P
+    assert _rel(q.qdd_mg_get_basis(g, nv, V), ref.basis()) <= 1e-3
+    v = inputs.gaussian_source(L44, 4006)
+    assert _rel(q.qdd_mg_vcycle(g, np.ascontiguousarray(v)), ref.vcycle(v)) <= 1e-3
+    with pytest.raises(q.QddError):
+        q.qdd_mg_setup(g, np.ascontiguousarray(w0), nv=nv, bootstrap=-1)
+    q.qdd_destroy_gauge(g)
+
+
 def test_vcycle_with_post_smoothing_matches_reference(q, ctx, ora):
     from oracle import mg
     U, A, Ainv, g = _problem(q, ctx, ora, L44, DOM2, 0.13)

@@ -2,9 +2,10 @@
 respects chirality and is orthonormal per block, its coarse operator keeps
 the gamma5-hermiticity of D, a complete basis makes the coarse correction
 the exact inverse (dense LU), the coarse correction removes every error in
-the range of P, and the multigrid-preconditioned FGMRES reaches the LU
+the range of P, the multigrid-preconditioned FGMRES reaches the LU
 solution in fewer steps than the Schwarz-preconditioned one near the
-critical kappa."""
+critical kappa, and a bootstrap pass without post-smoothing keeps the
+coarse space (the exact coarse correction does not change)."""
 import numpy as np
 import pytest
 
@@ -114,3 +115,20 @@ def test_multigrid_fgmres_reaches_lu_in_fewer_steps(ora, field):
     r = b.reshape(-1) - ora.apply_D(L44, U, A, kappa, x_mg.reshape(256, 4, 3)).reshape(-1)
     assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(b)
     assert info_mg["iters"] < info_sap["iters"]
+
+
+def test_bootstrap_without_smoothing_keeps_the_coarse_space(field):
+    """Without post-smoothing every V-cycle output lies in range(P), so a
+    bootstrap pass rebuilds P with the same span per block: the exact coarse
+    correction P D_c^{-1} P^H is unchanged, while the columns themselves
+    change.  A pass that rebuilt the wrong blocks, or left D_c stale, fails."""
+    M0 = _mg(field, 3, post_ncy=0)
+    M1 = _mg(field, 3, post_ncy=0, bootstrap=1)
+    assert np.abs(M1.basis() - M0.basis()).max() > 1e-3
+    v = inputs.gaussian_source(L44, 4010)
+    z0, z1 = M0.vcycle(v, exact_coarse=True), M1.vcycle(v, exact_coarse=True)
+    assert np.linalg.norm(z1 - z0) <= 1e-10 * np.linalg.norm(z0)
+    # with smoothing the span moves
+    M2 = _mg(field, 3, post_ncy=2, bootstrap=1)
+    M2.post_ncy = 0
+    assert np.linalg.norm(M2.vcycle(v, exact_coarse=True) - z0) > 1e-3 * np.linalg.norm(z0)
