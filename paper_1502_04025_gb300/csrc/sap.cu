@@ -134,13 +134,17 @@ struct SapArgs {
 
 __host__ __device__ constexpr size_t align128(size_t b) { return (b + 127) & ~(size_t)127; }
 
+// entries of the MR reduction buffer: 4 per warp when the half-field fills
+// whole warps, else one triple per thread (3 * Vh)
+__host__ __device__ constexpr int sap_red_elems(int Vh) { return (Vh % 32 == 0 || 3 * Vh <= 128) ? 128 : 3 * Vh; }
+
 template <typename R, typename SL, typename SC>
 __host__ __device__ constexpr size_t sap_smem_layout(int Vd, bool stl, bool stc)
 {
     return (stl ? align128((size_t)36 * Vd * sizeof(typename SL::T2)) : 0) +
            (stc ? align128((size_t)36 * Vd * sizeof(typename SC::T2)) : 0) +
            ((stc && SC::kScaled) ? align128((size_t)Vd * 4) : 0) + 3 * align128((size_t)12 * (Vd / 2) * sizeof(cpx<R>)) +
-           align128(128 * sizeof(R)) + align128(16);
+           align128((size_t)sap_red_elems(Vd / 2) * sizeof(R)) + align128(16);
 }
 
 template <typename R, typename SL, typename SC, typename SS, typename SP, bool STL, bool STC>
@@ -382,7 +386,7 @@ __global__ void __launch_bounds__(256) k_sap(const SapArgs<R, SL, SC, SS, SP> a)
     cpx<R> *sR = (cpx<R> *)ptr;   ptr += align128((size_t)12 * Vh * sizeof(cpx<R>));   // even half-field
     cpx<R> *sT = (cpx<R> *)ptr;   ptr += align128((size_t)12 * Vh * sizeof(cpx<R>));   // odd half-field
     cpx<R> *sRo = (cpx<R> *)ptr;  ptr += align128((size_t)12 * Vh * sizeof(cpx<R>));   // rho_o after inflow
-    R *sRed = (R *)ptr;           ptr += align128(128 * sizeof(R));
+    R *sRed = (R *)ptr;           ptr += align128((size_t)sap_red_elems(Vh) * sizeof(R));
     uint64_t *bar = (uint64_t *)ptr;  // [0]: links and clover staged, [1]: face slots staged
     // the face slots are staged over the odd half-fields sT and sRo (free at
     // the start of a visit) when they fit there; in FP32 only (FP64 would hold

@@ -66,6 +66,7 @@ GEOMS = [
     ((4, 4, 4, 4), (2, 2, 2, 2)),      # 8-site half domains: partial-warp reductions
     ((8, 4, 4, 12), (4, 2, 2, 2)),     # ragged: 6 blocks in t, 32-site domains
     ((16, 8, 8, 8), (8, 4, 4, 4)),     # 8x4^3 domains of 512 sites (config-2 shape)
+    ((12, 8, 4, 4), (6, 4, 2, 2)),     # 48-site half domains: one and a half warps per domain
 ]
 
 
@@ -158,7 +159,7 @@ def test_sap_f64_matches_oracle(q, ctx, ora, L, dom, n_half):
 
 
 @pytest.mark.parametrize("prec", ["f32", "h16", "f16", "bf16"])
-@pytest.mark.parametrize("L,dom", [GEOMS[0], GEOMS[3]])
+@pytest.mark.parametrize("L,dom", [GEOMS[0], GEOMS[3], GEOMS[4]])
 def test_sap_lowp_matches_oracle(q, ctx, ora, L, dom, prec):
     P = problem(q, ctx, ora, L, dom)
     eta = inputs.gaussian_source(L, 3002)

@@ -83,7 +83,7 @@ def _coords(L, n):
 
 @pytest.mark.parametrize("L,dom", [((8, 8, 8, 8), (4, 4, 4, 4)), ((4, 4, 4, 4), (2, 2, 2, 2)),
                                    ((8, 4, 4, 12), (4, 2, 2, 2)), ((16, 8, 8, 8), (8, 4, 4, 4)),
-                                   ((16, 16, 16, 32), (8, 4, 4, 4))])
+                                   ((16, 16, 16, 32), (8, 4, 4, 4)), ((12, 8, 4, 4), (6, 4, 2, 2))])
 def test_device_layout_tables(qdd, L, dom):
     """The neighbour tables the kernels use reproduce the periodic lattice
     neighbours, slots are colour-major and parity-split, and the
