@@ -187,6 +187,16 @@ qdd_status qdd_set_link_compression(qdd_gauge *g, int two_rows);
 qdd_status qdd_link_compression(qdd_gauge *g, int *two_rows, int *is_su3);
 
 /*
+ * Range-checked build (test aid; compute-sanitizer stands in elsewhere).
+ * A library built with -DQDD_CHECK (libqdd_check.so) tests the indices of
+ * the Schwarz kernel's stencil, face-slot and reduction accesses and of the
+ * full-lattice operators' neighbour reads; one out of range is counted and
+ * its access skipped.  *hits = the count since the library was loaded.  The
+ * normal build sets *hits = 0 and returns QDD_EINVAL.
+ */
+qdd_status qdd_check_hits(unsigned long long *hits);
+
+/*
  * Build the clover term A = 1 + i kappa c_sw sum sigma F (two Hermitian 6x6
  * chirality blocks per site) and the inverse blocks on odd sites used by the
  * even-odd domain solver (Sec. 3.1, footnote on the domain inversion).  Must

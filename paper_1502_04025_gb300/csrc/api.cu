@@ -421,6 +421,23 @@ qdd_status qdd_set_link_compression(qdd_gauge *g, int two_rows)
     return QDD_OK;
 }
 
+qdd_status qdd_check_hits(unsigned long long *hits)
+{
+    clear_error();
+    if (!hits) {
+        set_error("null argument");
+        return QDD_EINVAL;
+    }
+#ifdef QDD_CHECK
+    *hits = check_hits_sap() + check_hits_dslash();
+    return QDD_OK;
+#else
+    *hits = 0;
+    set_error("this library was built without range checks (QDD_CHECK)");
+    return QDD_EINVAL;
+#endif
+}
+
 qdd_status qdd_link_compression(qdd_gauge *g, int *two_rows, int *is_su3)
 {
     clear_error();

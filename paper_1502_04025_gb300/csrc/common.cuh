@@ -423,4 +423,21 @@ struct StDF {
 // Runtime-checked device error flags (bounded waits that ran out, etc.).
 constexpr int kErrMbarTimeout = 1;
 
+// Range checks of the hot-path kernels' indices.  A library built with
+// -DQDD_CHECK tests every guarded index; one out of range is counted in this
+// translation unit's counter and its access skipped (no trap, no wait).  In
+// the normal build the guard is the constant true and compiles away.
+#ifdef QDD_CHECK
+static __device__ unsigned long long g_check_hits;
+__device__ __forceinline__ bool in_range(long long v, long long lo, long long hi)
+{
+    if (v >= lo && v < hi) return true;
+    atomicAdd(&g_check_hits, 1ull);
+    return false;
+}
+#define QDD_IN_RANGE(v, lo, hi) ::qdd::in_range((long long)(v), (long long)(lo), (long long)(hi))
+#else
+#define QDD_IN_RANGE(v, lo, hi) true
+#endif
+
 }  // namespace qdd

@@ -59,17 +59,21 @@ __device__ __forceinline__ void dslash_dir(const Geom &g, const Field<SL> &U, co
         uint16_t e = __ldg(g.nbl + s * 8 + 2 * MU);
         int nd = (e & kCross) ? __ldg(g.nbd + d * 8 + 2 * MU) : d;
         int ns = e & kSlotMask;
-        load_spinor<R, SI>(in, rbase + (int64_t)nd * 12 * g.Vd + ns, sbase + (int64_t)nd * g.Vd + ns, g.Vd, x);
-        load_link<R, SL, L12>(U, d, s, MU, g.Vd, u);
-        hop<MU, +1>(u, x, acc);
+        if (QDD_IN_RANGE(nd, 0, g.Nd) && QDD_IN_RANGE(ns, 0, g.Vd)) {
+            load_spinor<R, SI>(in, rbase + (int64_t)nd * 12 * g.Vd + ns, sbase + (int64_t)nd * g.Vd + ns, g.Vd, x);
+            load_link<R, SL, L12>(U, d, s, MU, g.Vd, u);
+            hop<MU, +1>(u, x, acc);
+        }
     }
     {
         uint16_t e = __ldg(g.nbl + s * 8 + 2 * MU + 1);
         int nd = (e & kCross) ? __ldg(g.nbd + d * 8 + 2 * MU + 1) : d;
         int ns = e & kSlotMask;
-        load_spinor<R, SI>(in, rbase + (int64_t)nd * 12 * g.Vd + ns, sbase + (int64_t)nd * g.Vd + ns, g.Vd, x);
-        load_link<R, SL, L12>(U, nd, ns, MU, g.Vd, u);
-        hop<MU, -1>(u, x, acc);
+        if (QDD_IN_RANGE(nd, 0, g.Nd) && QDD_IN_RANGE(ns, 0, g.Vd)) {
+            load_spinor<R, SI>(in, rbase + (int64_t)nd * 12 * g.Vd + ns, sbase + (int64_t)nd * g.Vd + ns, g.Vd, x);
+            load_link<R, SL, L12>(U, nd, ns, MU, g.Vd, u);
+            hop<MU, -1>(u, x, acc);
+        }
     }
 }
 
@@ -255,6 +259,7 @@ __global__ void __launch_bounds__(128, 4) k_dslash_df(Geom g, const float4 *U, c
         uint16_t e = __ldg(g.nbl + s * 8 + dir);
         int nd = (e & kCross) ? __ldg(g.nbd + d * 8 + dir) : d;
         int ns = e & kSlotMask;
+        if (!(QDD_IN_RANGE(nd, 0, g.Nd) && QDD_IN_RANGE(ns, 0, g.Vd))) continue;
         cdf x[12], u[9];
         const typename SI::T2 *xp = in + rbase + (int64_t)nd * 12 * g.Vd + ns;
 #pragma unroll
@@ -312,6 +317,18 @@ __global__ void __launch_bounds__(128, 4) k_dslash_df(Geom g, const float4 *U, c
             hv[i] = hv[6 + i];
         }
     }
+}
+
+// out-of-range indices the kernels of this file have skipped (QDD_CHECK builds)
+unsigned long long check_hits_dslash()
+{
+#ifdef QDD_CHECK
+    unsigned long long h = 0;
+    if (cudaMemcpyFromSymbol(&h, g_check_hits, sizeof(h)) != cudaSuccess) return ~0ull;
+    return h;
+#else
+    return 0;
+#endif
 }
 
 template <typename R, typename SL, typename SC, typename SI, typename SO, bool RESID, bool L12 = false>

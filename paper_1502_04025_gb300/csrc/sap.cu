@@ -201,7 +201,7 @@ struct SapBlock {
     {
         cpx<R> u[9], x[12];
         uint16_t e = nb[2 * MU];
-        if (!(e & kCross)) {
+        if (!(e & kCross) && QDD_IN_RANGE((e & kSlotMask) - src_off, 0, Vh)) {
             int ns = (e & kSlotMask) - src_off;
 #pragma unroll
             for (int k = 0; k < 12; k++) x[k] = src[k * Vh + ns];
@@ -209,7 +209,7 @@ struct SapBlock {
             hop<MU, +1>(u, x, acc);
         }
         e = nb[2 * MU + 1];
-        if (!(e & kCross)) {
+        if (!(e & kCross) && QDD_IN_RANGE((e & kSlotMask) - src_off, 0, Vh)) {
             int ns = e & kSlotMask;
 #pragma unroll
             for (int k = 0; k < 12; k++) x[k] = src[k * Vh + ns - src_off];
@@ -231,7 +231,8 @@ struct SapBlock {
     {
         const int nf = a.g.nf, t = (fc >> (8 * MU)) & 255;
         cpx<R> h[6];
-        if (nb[2 * MU] & kCross) {
+        if ((nb[2 * MU] & kCross) && QDD_IN_RANGE(nbd[2 * MU], 0, a.g.Nd) &&
+            QDD_IN_RANGE(a.g.foff[2 * MU + 1] + t, 0, nf)) {
             cpx<R> u[9], w[6];
             project<MU, -1>(dl, h);
             link(d, s, MU, u);
@@ -240,7 +241,8 @@ struct SapBlock {
 #pragma unroll
             for (int k = 0; k < 6; k++) dst[k * nf] = w[k];
         }
-        if (nb[2 * MU + 1] & kCross) {
+        if ((nb[2 * MU + 1] & kCross) && QDD_IN_RANGE(nbd[2 * MU + 1], 0, a.g.Nd) &&
+            QDD_IN_RANGE(a.g.foff[2 * MU] + t, 0, nf)) {
             project<MU, +1>(dl, h);
             cpx<R> *dst = fb + (int64_t)nbd[2 * MU + 1] * 6 * nf + a.g.foff[2 * MU] + t;
 #pragma unroll
@@ -281,7 +283,7 @@ __device__ __forceinline__ void face_in_dir(const Geom &g, const uint16_t *nb, u
 {
     const int t = (fc >> (8 * MU)) & 255;
     cpx<R> h[6];
-    if (nb[2 * MU] & kCross) {
+    if ((nb[2 * MU] & kCross) && QDD_IN_RANGE(g.foff[2 * MU] + t, 0, g.nf)) {
         const cpx<R> *src = fd + g.foff[2 * MU] + t;
 #pragma unroll
         for (int k = 0; k < 6; k++) h[k] = src[k * g.nf];
@@ -290,7 +292,7 @@ __device__ __forceinline__ void face_in_dir(const Geom &g, const uint16_t *nb, u
         su3_mul_half<false>(u, h, w);
         reconstruct_add<MU, +1>(w, acc);
     }
-    if (nb[2 * MU + 1] & kCross) {
+    if ((nb[2 * MU + 1] & kCross) && QDD_IN_RANGE(g.foff[2 * MU + 1] + t, 0, g.nf)) {
         const cpx<R> *src = fd + g.foff[2 * MU + 1] + t;
 #pragma unroll
         for (int k = 0; k < 6; k++) h[k] = src[k * g.nf];
@@ -606,16 +608,18 @@ __global__ void __launch_bounds__(256) k_sap(const SapArgs<R, SL, SC, SS, SP> a)
                     pr_re = warp_sum(pr_re);
                     pr_im = warp_sum(pr_im);
                     pp = warp_sum(pp);
-                    if ((i & 31) == 0) {
+                    if ((i & 31) == 0 && QDD_IN_RANGE((i >> 5) * 4 + 2, 0, sap_red_elems(Vh))) {
                         sRed[(i >> 5) * 4 + 0] = pr_re;
                         sRed[(i >> 5) * 4 + 1] = pr_im;
                         sRed[(i >> 5) * 4 + 2] = pp;
                     }
                 } else {
-                    // partial warp (Vh < 32): per-thread partials, summed in order below
-                    sRed[i * 3 + 0] = pr_re;
-                    sRed[i * 3 + 1] = pr_im;
-                    sRed[i * 3 + 2] = pp;
+                    // partial warp: per-thread partials, summed in order below
+                    if (QDD_IN_RANGE(i * 3 + 2, 0, sap_red_elems(Vh))) {
+                        sRed[i * 3 + 0] = pr_re;
+                        sRed[i * 3 + 1] = pr_im;
+                        sRed[i * 3 + 2] = pp;
+                    }
                 }
                 __syncthreads();
                 R tr = 0, ti_ = 0, tp = 0;
@@ -789,6 +793,18 @@ static qdd_status dispatch_staging(Gauge *g, const SapArgs<R, SL, SC, SS, SP> &a
         return run_sap<R, SL, SC, SS, SP, false, false>(g, a, s, pdl, timed);
     set_error("domain of %d sites does not fit in shared memory", Vd);
     return QDD_EINVAL;
+}
+
+// out-of-range indices the kernels of this file have skipped (QDD_CHECK builds)
+unsigned long long check_hits_sap()
+{
+#ifdef QDD_CHECK
+    unsigned long long h = 0;
+    if (cudaMemcpyFromSymbol(&h, g_check_hits, sizeof(h)) != cudaSuccess) return ~0ull;
+    return h;
+#else
+    return 0;
+#endif
 }
 
 size_t sap_face_bytes(const HostGeom &hg, qdd_prec prec, int nrhs)

@@ -16,7 +16,8 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libqdd.so")
+# QDD_CHECKED=1 loads the range-checked build of the same library (tests)
+LIB_PATH = os.path.join(HERE, "libqdd_check.so" if os.environ.get("QDD_CHECKED") == "1" else "libqdd.so")
 
 QDD_OK, QDD_EINVAL, QDD_ENOMEM, QDD_EBUDGET, QDD_ENOCONV, QDD_ENAN, QDD_ETIMEOUT, QDD_ECUDA, QDD_ENOTREADY = range(9)
 QDD_PREC_F64, QDD_PREC_F32, QDD_PREC_F16S, QDD_PREC_BF16S, QDD_PREC_DF64, QDD_PREC_H16 = range(6)
@@ -26,7 +27,7 @@ STATUS_NAMES = ["QDD_OK", "QDD_EINVAL", "QDD_ENOMEM", "QDD_EBUDGET", "QDD_ENOCON
                 "QDD_ECUDA", "QDD_ENOTREADY"]
 
 if not os.path.exists(LIB_PATH):
-    raise ImportError(f"libqdd.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+    raise ImportError(f"{os.path.basename(LIB_PATH)} is not built ({LIB_PATH}); run __graft_entry__.build()")
 
 
 class qdd_solve_params(ctypes.Structure):
@@ -78,6 +79,7 @@ _SIGS = {
     "qdd_destroy_gauge": (None, [_vp]),
     "qdd_set_link_compression": (ctypes.c_int, [_vp, ctypes.c_int]),
     "qdd_link_compression": (ctypes.c_int, [_vp, _ip, _ip]),
+    "qdd_check_hits": (ctypes.c_int, [ctypes.POINTER(ctypes.c_ulonglong)]),
     "qdd_set_clover": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double]),
     "qdd_get_clover": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
     "qdd_apply_D": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp]),
@@ -226,6 +228,14 @@ def qdd_link_compression(g):
     t, u = ctypes.c_int(), ctypes.c_int()
     _check(_lib.qdd_link_compression(g, ctypes.byref(t), ctypes.byref(u)), "qdd_link_compression")
     return bool(t.value), bool(u.value)
+
+
+def qdd_check_hits() -> int:
+    """Out-of-range indices the range-checked build has skipped (raises
+    QddError with the normal build)."""
+    h = ctypes.c_ulonglong()
+    _check(_lib.qdd_check_hits(ctypes.byref(h)), "qdd_check_hits")
+    return h.value
 
 
 def qdd_set_clover(g, c_sw: float, kappa: float):

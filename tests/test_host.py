@@ -74,6 +74,9 @@ def test_working_set_pins(qdd):
 def test_no_gpu_needed_for_errors(qdd):
     # a null context is rejected without touching the device
     assert qdd._lib.qdd_set_profiling(None, 1) == qdd.QDD_EINVAL
+    # the normal build has no range checks to report
+    with pytest.raises(qdd.QddError):
+        qdd.qdd_check_hits()
 
 
 def _coords(L, n):
