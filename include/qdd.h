@@ -189,8 +189,9 @@ qdd_status qdd_link_compression(qdd_gauge *g, int *two_rows, int *is_su3);
 /*
  * Range-checked build (test aid; compute-sanitizer stands in elsewhere).
  * A library built with -DQDD_CHECK (libqdd_check.so) tests the indices of
- * the Schwarz kernel's stencil, face-slot and reduction accesses and of the
- * full-lattice operators' neighbour reads; one out of range is counted and
+ * the Schwarz kernel's stencil, face-slot and reduction accesses, of the
+ * full-lattice operators' neighbour reads and of the multigrid kernels'
+ * neighbour-domain reads; one out of range is counted and
  * its access skipped.  *hits = the count since the library was loaded.  The
  * normal build sets *hits = 0 and returns QDD_EINVAL.
  */

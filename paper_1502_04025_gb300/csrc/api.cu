@@ -429,7 +429,7 @@ qdd_status qdd_check_hits(unsigned long long *hits)
         return QDD_EINVAL;
     }
 #ifdef QDD_CHECK
-    *hits = check_hits_sap() + check_hits_dslash();
+    *hits = check_hits_sap() + check_hits_dslash() + check_hits_mg();
     return QDD_OK;
 #else
     *hits = 0;

@@ -143,6 +143,7 @@ __device__ __forceinline__ void mg_hops_dir(const Geom &g, const Field<StF32> &U
         const bool cross = (e & kCross) != 0;
         if (crossing_only ? (dir != only_dir || !cross) : cross) continue;
         const int nd = cross ? __ldg(g.nbd + d * 8 + dir) : d, ns = e & kSlotMask;
+        if (!(QDD_IN_RANGE(nd, 0, g.Nd) && QDD_IN_RANGE(ns, 0, g.Vd))) continue;
         cpx<float> x[12], u[9];
         B.load(j, nd, ns, x);
         const float2 *up = U.p + ((int64_t)(b ? nd : d) * 36 + MU * 9) * g.Vd + (b ? ns : s);
@@ -311,8 +312,8 @@ __global__ void __launch_bounds__(288) k_mg_coarse_apply(const float2 *Y, const 
     if (*done) return;  // the coarse cycle has broken down exactly: nothing left to do
     const int d = blockIdx.x, n = threadIdx.x >> 5, i = threadIdx.x & 31;
     float re = 0.f, im = 0.f;
-    if (i < nc) {
-        const int dn = n == 0 ? d : __ldg(nbd + d * 8 + n - 1);
+    const int dn = (i < nc) ? (n == 0 ? d : __ldg(nbd + d * 8 + n - 1)) : d;
+    if (i < nc && QDD_IN_RANGE(dn, 0, gridDim.x)) {
         const float2 *blk = Y + ((int64_t)d * 9 + n) * nc * nc + i;
         const float2 *xv = x + (int64_t)dn * nc;
 #pragma unroll 8
@@ -719,6 +720,18 @@ static qdd_status mg_build(Gauge *g, Multigrid &M, double2 *w64, cudaStream_t s)
 }
 
 qdd_prec mg_smoother_prec(const Gauge *g) { return g->mg ? g->mg->p.sap_prec : QDD_PREC_F32; }
+
+// out-of-range indices the kernels of this file have skipped (QDD_CHECK builds)
+unsigned long long check_hits_mg()
+{
+#ifdef QDD_CHECK
+    unsigned long long h = 0;
+    if (cudaMemcpyFromSymbol(&h, g_check_hits, sizeof(h)) != cudaSuccess) return ~0ull;
+    return h;
+#else
+    return 0;
+#endif
+}
 
 static qdd_status mg_check(const qdd_mg_params *p)
 {
