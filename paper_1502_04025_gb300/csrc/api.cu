@@ -185,7 +185,7 @@ qdd_status ensure_copy(Gauge *g, qdd_prec prec, cudaStream_t s)
         QDD_TRY(c.sclov_s.ensure(g->ctx, V * 4));
     }
     QDD_TRY(launch_links_convert(g, prec, c.links.p, s));
-    QDD_TRY(launch_clover_convert(g, g->clov64.as<double2>(), prec, c.clov.p, c.clov_s.as<float>(), s));
+    QDD_TRY(launch_clover_convert(g, g->clov64.as<double2>(), prec, c.clov.p, c.clov_s.as<float>(), s, true));
     QDD_TRY(launch_clover_convert(g, g->sclov64.as<double2>(), prec, c.sclov.p, c.sclov_s.as<float>(), s));
     c.valid = true;
     return QDD_OK;

@@ -30,6 +30,26 @@ __device__ __forceinline__ void load_spinor(const Field<S> &f, int64_t gi_plane_
     }
 }
 
+// Two adjacent planes of a paired 16-bit field with one 8-byte load.
+template <typename R>
+__device__ __forceinline__ void ld_pair(const __half2 *p, cpx<R> &a, cpx<R> &b)
+{
+    uint2 v = __ldg(reinterpret_cast<const uint2 *>(p));
+    float2 f0 = __half22float2(*reinterpret_cast<const __half2 *>(&v.x));
+    float2 f1 = __half22float2(*reinterpret_cast<const __half2 *>(&v.y));
+    a = mk<R>(f0.x, f0.y);
+    b = mk<R>(f1.x, f1.y);
+}
+template <typename R>
+__device__ __forceinline__ void ld_pair(const __nv_bfloat162 *p, cpx<R> &a, cpx<R> &b)
+{
+    uint2 v = __ldg(reinterpret_cast<const uint2 *>(p));
+    float2 f0 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&v.x));
+    float2 f1 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&v.y));
+    a = mk<R>(f0.x, f0.y);
+    b = mk<R>(f1.x, f1.y);
+}
+
 // Link U_mu of site s of domain d.  L12: the field holds the first two rows
 // (24 planes per site) and the third is rebuilt as the conjugated cross
 // product of the two, i.e. from the cofactors of U = (U^+)^-1 for det U = 1.
@@ -37,9 +57,15 @@ template <typename R, typename S, bool L12>
 __device__ __forceinline__ void load_link(const Field<S> &U, int d, int s, int mu, int Vd, cpx<R> *u)
 {
     if (L12) {
-        const typename S::T2 *p = U.p + ((int64_t)d * 24 + mu * 6) * Vd + s;
+        if constexpr (S::kBytes == 4) {  // 16-bit: paired planes
+            const typename S::T2 *p = U.p + pair_index(d, 24, mu * 6, Vd, s);
 #pragma unroll
-        for (int k = 0; k < 6; k++) u[k] = ld_c<R>(p + (int64_t)k * Vd);
+            for (int j = 0; j < 3; j++) ld_pair<R>(p + (int64_t)j * Vd * 2, u[2 * j], u[2 * j + 1]);
+        } else {
+            const typename S::T2 *p = U.p + ((int64_t)d * 24 + mu * 6) * Vd + s;
+#pragma unroll
+            for (int k = 0; k < 6; k++) u[k] = ld_c<R>(p + (int64_t)k * Vd);
+        }
         u[6] = conj(u[1] * u[5] - u[2] * u[4]);
         u[7] = conj(u[2] * u[3] - u[0] * u[5]);
         u[8] = conj(u[0] * u[4] - u[1] * u[3]);
@@ -105,10 +131,17 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 1) k_dslash(Geom g, 
 #pragma unroll
         for (int blk = 0; blk < 2; blk++) {
             cpx<R> m[18];
+            if constexpr (SC::kBytes == 4) {  // 16-bit: paired planes
+                const typename SC::T2 *pp = A.p + pair_index(d, 36, blk * 18, g.Vd, s);
 #pragma unroll
-            for (int k = 0; k < 18; k++) {
-                cpx<R> v = ld_c<R>(p + (int64_t)(blk * 18 + k) * g.Vd);
-                m[k] = SC::kScaled ? sc * v : v;
+                for (int j = 0; j < 9; j++) ld_pair<R>(pp + (int64_t)j * g.Vd * 2, m[2 * j], m[2 * j + 1]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 18; k++) m[k] = ld_c<R>(p + (int64_t)(blk * 18 + k) * g.Vd);
+            }
+            if (SC::kScaled) {
+#pragma unroll
+                for (int k = 0; k < 18; k++) m[k] = sc * m[k];
             }
             herm6_mul(m, x + 6 * blk, y + 6 * blk);
         }

@@ -206,6 +206,14 @@ struct Fields {
     Field<S> U, A, C;  // links, clover, Schwarz clover
 };
 
+// Paired-plane order of a 16-bit field read only by the full-lattice
+// operator: planes 2q and 2q+1 of a site are adjacent (one 8-byte load).
+// Element index of plane p of site s in domain d, for P planes per site.
+__host__ __device__ __forceinline__ int64_t pair_index(int64_t d, int P, int p, int Vd, int s)
+{
+    return (((int64_t)d * (P / 2) + p / 2) * Vd + s) * 2 + (p & 1);
+}
+
 qdd_status ensure_copy(Gauge *g, qdd_prec prec, cudaStream_t s);
 // the two-row link copy of a storage precision (FP32, FP16, BF16)
 qdd_status ensure_links12(Gauge *g, qdd_prec prec, cudaStream_t s);
@@ -234,8 +242,9 @@ qdd_status launch_spinor_convert(Gauge *g, const void *src, const float *src_sca
                                  float *dst_scale, qdd_prec dp, int nrhs, cudaStream_t s);
 // plane-wise down-conversion of links (unscaled) / clover (per-site scale)
 qdd_status launch_links_convert(Gauge *g, qdd_prec dp, void *dst, cudaStream_t s);
+// paired: the full-lattice operator's copy (16-bit formats in paired-plane order)
 qdd_status launch_clover_convert(Gauge *g, const double2 *src, qdd_prec dp, void *dst, float *dst_scale,
-                                 cudaStream_t s);
+                                 cudaStream_t s, bool paired = false);
 // *d_bad = 1 when some link is not SU(3) to tol; two-row copy of the links
 qdd_status launch_su3_check(Gauge *g, double tol, int *d_bad, cudaStream_t s);
 qdd_status launch_links12_convert(Gauge *g, qdd_prec dp, void *dst, cudaStream_t s);

@@ -305,7 +305,9 @@ __global__ void k_su3_check(Geom g, const double2 *U, double tol, int *bad)
 }
 
 // The first two rows of every link: 24 planes per site, plane mu*6 + 3*row + col
-// (an SU(3) link's third row is the conjugated cross product of the two)
+// (an SU(3) link's third row is the conjugated cross product of the two).
+// 16-bit formats are stored with planes paired (pair_index below), so that
+// the operator reads two planes with one 8-byte load.
 template <typename S>
 __global__ void k_links12_convert(Geom g, const double2 *src, typename S::T2 *dst)
 {
@@ -316,13 +318,16 @@ __global__ void k_links12_convert(Geom g, const double2 *src, typename S::T2 *ds
     for (int mu = 0; mu < 4; mu++)
         for (int k = 0; k < 6; k++) {
             double2 a = __ldg(src + ((int64_t)d * 36 + mu * 9 + k) * g.Vd + s);
-            st_c<double>(dst + ((int64_t)d * 24 + mu * 6 + k) * g.Vd + s, mk(a.x, a.y));
+            const int p = mu * 6 + k;
+            st_c<double>(dst + (S::kBytes == 4 ? pair_index(d, 24, p, g.Vd, s) : ((int64_t)d * 24 + p) * g.Vd + s),
+                         mk(a.x, a.y));
         }
 }
 
 // clover blocks: 36 planes per site; 16-bit formats get one scale per site
+// (paired: planes stored in pairs, for the full-lattice operator's copy)
 template <typename S>
-__global__ void k_clover_convert(Geom g, const double2 *src, Field<S> dst)
+__global__ void k_clover_convert(Geom g, const double2 *src, Field<S> dst, int paired)
 {
     int gi = blockIdx.x * blockDim.x + threadIdx.x;
     if (gi >= g.V) return;
@@ -343,7 +348,8 @@ __global__ void k_clover_convert(Geom g, const double2 *src, Field<S> dst)
     }
     for (int k = 0; k < 36; k++) {
         double2 a = __ldg(p + (int64_t)k * g.Vd);
-        st_c<double>(q + (int64_t)k * g.Vd, mk(a.x * inv, a.y * inv));
+        typename S::T2 *o = paired ? dst.p + pair_index(d, 36, k, g.Vd, s) : q + (int64_t)k * g.Vd;
+        st_c<double>(o, mk(a.x * inv, a.y * inv));
     }
 }
 
@@ -459,12 +465,13 @@ qdd_status launch_split_convert(Gauge *g, const double2 *src, float4 *dst, int64
 }
 
 qdd_status launch_clover_convert(Gauge *g, const double2 *src, qdd_prec dp, void *dst, float *dst_scale,
-                                 cudaStream_t s)
+                                 cudaStream_t s, bool paired)
 {
     LaunchScope ls(g->ctx->timer, K_OTHER, s);
     QDD_DISPATCH_PREC(dp, S, {
         Field<S> f{(typename S::T2 *)dst, dst_scale};
-        k_clover_convert<S><<<grid_sites(g->hg.V, 1, 256), 256, 0, s>>>(g->geom, src, f);
+        k_clover_convert<S><<<grid_sites(g->hg.V, 1, 256), 256, 0, s>>>(g->geom, src, f,
+                                                                         paired && S::kBytes == 4 ? 1 : 0);
     });
     QDD_CUDA(cudaGetLastError());
     return QDD_OK;
