@@ -251,32 +251,66 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_coarse_build(Geom g, Field<St
 
 // ------------------------------------------------------------ transfer
 
-// rc[d][chi * nv + k] = <P_(d,chi,k), v>, one CTA per aggregate
-template <typename T2>
-__global__ void __launch_bounds__(kMgThreads) k_mg_restrict(const float2 *P, int nv, int64_t stride, int Vd,
-                                                            const T2 *v, float2 *rc)
+// rc[d][chi * nv + k] = <P_(d,chi,k), v>, one CTA per aggregate.  Each
+// thread reads its entries of v once and accumulates all NV products (v is
+// read once, P once); warp shuffles, then a fixed-order sum over the warps.
+template <int NV, typename T2>
+__global__ void __launch_bounds__(kMgThreads) k_mg_restrict(const float2 *P, int64_t stride, int Vd, const T2 *v,
+                                                            float2 *rc)
 {
-    // the 2 nv dot products in parallel, one warp each (shuffle sums only)
+    __shared__ float2 part[kMgThreads / 32][NV];
     const int d = blockIdx.x, n = 6 * Vd;
-    const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
-    for (int t = threadIdx.x >> 5; t < 2 * nv; t += nwarp) {
-        const int chi = t / nv, k = t % nv;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int chi = 0; chi < 2; chi++) {
         const int64_t base = (int64_t)d * 12 * Vd + (int64_t)6 * chi * Vd;
-        float px = 0.f, py = 0.f;
-#pragma unroll 8
-        for (int e = lane; e < n; e += 32) {
-            float2 a = __ldg(P + k * stride + base + e);
-            T2 b = v[base + e];
+        float px[NV], py[NV];
+#pragma unroll
+        for (int k = 0; k < NV; k++) px[k] = py[k] = 0.f;
+        for (int e = threadIdx.x; e < n; e += blockDim.x) {
+            const T2 b = v[base + e];
             const float bx = (float)b.x, by = (float)b.y;
-            px = fmaf(a.x, bx, fmaf(a.y, by, px));
-            py = fmaf(a.x, by, fmaf(-a.y, bx, py));
+#pragma unroll
+            for (int k = 0; k < NV; k++) {
+                const float2 a = __ldg(P + k * stride + base + e);
+                px[k] = fmaf(a.x, bx, fmaf(a.y, by, px[k]));
+                py[k] = fmaf(a.x, by, fmaf(-a.y, bx, py[k]));
+            }
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            px += __shfl_xor_sync(0xffffffffu, px, o);
-            py += __shfl_xor_sync(0xffffffffu, py, o);
+        for (int k = 0; k < NV; k++) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                px[k] += __shfl_xor_sync(0xffffffffu, px[k], o);
+                py[k] += __shfl_xor_sync(0xffffffffu, py[k], o);
+            }
+            if (lane == 0) part[w][k] = make_float2(px[k], py[k]);
         }
-        if (lane == 0) rc[(int64_t)d * 2 * nv + t] = make_float2(px, py);
+        __syncthreads();
+        if (threadIdx.x < NV) {
+            float2 t = part[0][threadIdx.x];
+            for (int ww = 1; ww < nw; ww++) {
+                t.x += part[ww][threadIdx.x].x;
+                t.y += part[ww][threadIdx.x].y;
+            }
+            rc[(int64_t)d * 2 * NV + chi * NV + threadIdx.x] = t;
+        }
+        __syncthreads();  // part is rewritten for the other chirality
+    }
+}
+
+template <typename T2>
+static void launch_mg_restrict(int nv, int nd, const float2 *P, int64_t stride, int Vd, const T2 *v, float2 *rc,
+                               cudaStream_t s)
+{
+    switch (nv) {
+#define QDD_MG_RESTRICT(N) \
+    case N: k_mg_restrict<N, T2><<<nd, kMgThreads, 0, s>>>(P, stride, Vd, v, rc); break;
+        QDD_MG_RESTRICT(1) QDD_MG_RESTRICT(2) QDD_MG_RESTRICT(3) QDD_MG_RESTRICT(4)
+        QDD_MG_RESTRICT(5) QDD_MG_RESTRICT(6) QDD_MG_RESTRICT(7) QDD_MG_RESTRICT(8)
+        QDD_MG_RESTRICT(9) QDD_MG_RESTRICT(10) QDD_MG_RESTRICT(11) QDD_MG_RESTRICT(12)
+        QDD_MG_RESTRICT(13) QDD_MG_RESTRICT(14) QDD_MG_RESTRICT(15) QDD_MG_RESTRICT(16)
+#undef QDD_MG_RESTRICT
+    default: break;  // nv is checked to be 1..16 at setup
     }
 }
 
@@ -661,8 +695,7 @@ static qdd_status mg_vcycle_with(Gauge *g, Multigrid &M, const double2 *v, void 
     const int64_t stride = nfine;
     {
         LaunchScope ls(g->ctx->timer, K_SAP, s);
-        k_mg_restrict<double2><<<g->hg.Nd, kMgThreads, 0, s>>>(M.P.as<float2>(), M.nv, stride, g->hg.Vd, v,
-                                                              M.cb.as<float2>());
+        launch_mg_restrict<double2>(M.nv, g->hg.Nd, M.P.as<float2>(), stride, g->hg.Vd, v, M.cb.as<float2>(), s);
         QDD_CUDA(cudaGetLastError());
     }
     QDD_TRY(mg_coarse_solve(g, M, s));
