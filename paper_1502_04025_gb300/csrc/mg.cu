@@ -622,6 +622,8 @@ struct Multigrid {
     // coarse GMRES basis and scalars
     DevMem t64, r64, rho, rho_s, face, err;
     DevMem cV, cx, cb, cst;  // coarse GMRES basis (coarse_iters + 1 vectors), solution, rhs, CgState
+    DevMem api_v, api_z, api_io;  // qdd_mg_vcycle's input, output and host-transfer buffers (kept, so
+                                  // that a call allocates and frees nothing after the first)
     cudaStream_t cap = nullptr;       // stream the coarse cycle was captured on
     cudaGraph_t graph = nullptr;      // the coarse cycle: init, coarse_iters x (stencil, step), finish
     cudaGraphExec_t exec = nullptr;
@@ -912,12 +914,13 @@ qdd_status qdd_mg_vcycle(qdd_gauge *g, const double *v, double *z, int on_device
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t nfine = (int64_t)g->hg.V * 12;
     const qdd_prec zp = g->mg->p.sap_prec == QDD_PREC_F64 ? QDD_PREC_F64 : QDD_PREC_F32;
-    DevMem io, vin, zt;
-    QDD_TRY(vin.alloc(ctx, nfine * sizeof(double2)));
-    QDD_TRY(zt.alloc(ctx, nfine * ebytes(zp)));
+    Multigrid &M = *g->mg;
+    DevMem &io = M.api_io, &vin = M.api_v, &zt = M.api_z;
+    QDD_TRY(vin.ensure(ctx, nfine * sizeof(double2)));
+    QDD_TRY(zt.ensure(ctx, nfine * ebytes(zp)));
     const double *src = v;
     if (!on_device) {
-        QDD_TRY(io.alloc(ctx, nfine * sizeof(double2)));
+        QDD_TRY(io.ensure(ctx, nfine * sizeof(double2)));
         QDD_CUDA(cudaMemcpyAsync(io.p, v, nfine * sizeof(double2), cudaMemcpyHostToDevice, s));
         src = io.as<double>();
     }
@@ -925,7 +928,7 @@ qdd_status qdd_mg_vcycle(qdd_gauge *g, const double *v, double *z, int on_device
     QDD_TRY(mg_vcycle(g, vin.as<double2>(), zt.p, zp, s));
     double *dst = z;
     if (!on_device) {
-        if (!io.p) QDD_TRY(io.alloc(ctx, nfine * sizeof(double2)));
+        QDD_TRY(io.ensure(ctx, nfine * sizeof(double2)));
         dst = io.as<double>();
     }
     QDD_TRY(launch_spinor_out(g, zt.p, nullptr, dst, zp, 1, s));
