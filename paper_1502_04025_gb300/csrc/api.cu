@@ -136,8 +136,6 @@ void DevMem::release()
     bytes = 0;
 }
 
-Gauge::~Gauge() = default;
-
 // -------------------------------------------------------- precision copies
 
 static size_t elem_bytes(qdd_prec p)
@@ -211,6 +209,8 @@ qdd_status ensure_links12(Gauge *g, qdd_prec prec, cudaStream_t s)
 struct Staging {
     DevMem io, a, a_s, b, b_s, c, c_s, err;
 };
+
+Gauge::~Gauge() = default;
 
 static qdd_status stage_in(Gauge *g, DevMem &io, const double *src, int nrhs, int on_device, cudaStream_t s,
                            const double **dev)
@@ -533,8 +533,7 @@ qdd_status qdd_apply_D(qdd_gauge *g, const double *in, double *out, int nrhs, qd
     std::lock_guard<std::mutex> lk(g->mu);
     QDD_CUDA(cudaSetDevice(g->ctx->device));
     cudaStream_t s = (cudaStream_t)stream;
-    static thread_local std::map<Gauge *, std::unique_ptr<Staging>> stg;
-    auto &st = stg[g];
+    auto &st = g->stage;  // under g->mu
     if (!st) st.reset(new Staging());
     const size_t V = g->hg.V;
     const size_t eb = elem_bytes(spinor_store(prec));
@@ -571,8 +570,7 @@ qdd_status qdd_sap_apply(qdd_gauge *g, const double *eta, double *psi, double *r
     std::lock_guard<std::mutex> lk(g->mu);
     QDD_CUDA(cudaSetDevice(g->ctx->device));
     cudaStream_t s = (cudaStream_t)stream;
-    static thread_local std::map<Gauge *, std::unique_ptr<Staging>> stg;
-    auto &st = stg[g];
+    auto &st = g->stage;  // under g->mu
     if (!st) st.reset(new Staging());
     const size_t V = g->hg.V;
     const qdd_prec ssp = spinor_store(prec);                                 // rho storage

@@ -194,6 +194,7 @@ struct Gauge {
     DevMem clov64, sclov64;   // FP64 clover A and Schwarz form (A even, A^-1 odd)
     PrecCopy copies[5];       // index = qdd_prec; F64 entry aliases the masters
     std::unique_ptr<Workspace> ws;  // workspace of the synchronous entry points
+    std::unique_ptr<struct Staging> stage;  // buffers of apply_D / sap_apply, freed with the gauge
     std::shared_ptr<struct Multigrid> mg;  // two-level multigrid preconditioner (qdd_mg_setup)
     std::mutex mu;            // one synchronous call at a time per gauge object
     std::mutex copy_mu;       // guards the lazily built precision copies
