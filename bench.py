@@ -145,7 +145,7 @@ class Clocks:
                 ["nvidia-smi", "-i", str(self.index),
                  "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,utilization.gpu",
                  "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
@@ -160,7 +160,7 @@ class Clocks:
             self.p.kill()
         self.f.flush()
         self.f.seek(0)
-        sm, mx, reasons = [], [], set()
+        sm, mx, util, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in self.f.read().splitlines():
             parts = [x.strip() for x in line.split(",")]
@@ -174,9 +174,14 @@ class Clocks:
             for n, v in zip(names, parts[5:9]):
                 if v.lower() == "active":
                     reasons.add(n)
+            try:
+                util.append(float(parts[9]))  # % of the sample period with a kernel running
+            except (IndexError, ValueError):
+                pass
         os.unlink(self.f.name)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "gpu_busy_fraction": statistics.mean(util) / 100 if util else None}
 
 
 def ncu_traffic(kernel):
@@ -746,6 +751,8 @@ def run_serve(args):
 
     th = threading.Thread(target=poller, daemon=True)
     th.start()
+    clocks = Clocks(0)
+    clocks.start()
     t_start = time.perf_counter()
     t_next = t_start
     for i, (li, ki, r) in enumerate(reqs):
@@ -761,11 +768,13 @@ def run_serve(args):
     done.wait()
     ok = ok[0]
     wall = time.perf_counter() - t_start
+    clk = clocks.stop()
     used, budget = qdd.qdd_memory(ctx)
     line = {"metric": "SAP-FGMRES serving latency (submit to result)", "value": float(np.percentile(lat, 50)) * 1e3,
             "unit": "ms", "higher_is_better": False, "p50_ms": float(np.percentile(lat, 50)) * 1e3,
             "p99_ms": float(np.percentile(lat, 99)) * 1e3, "solves_per_s": ok / wall, "requests": n,
-            "converged": ok, "failures": failures, "offered_rate_per_s": rate, "wall_s": wall, "data": "synthetic",
+            "converged": ok, "failures": failures, "offered_rate_per_s": rate, "wall_s": wall,
+            "gpu_busy_fraction": clk.get("gpu_busy_fraction"), "clocks": clk, "data": "synthetic",
             "config": {"workload": "serving mix: Poisson arrivals, lattices 8^4/16^3x32/24^3x48/32^3x64, "
                                    "kappa in {0.120,0.125,0.130,0.135}, 1-12 rhs, FP32 SAP, tol 1e-10",
                        "slots": 4, "hbm_budget_bytes": budget, "resident_gauge_bytes": used},

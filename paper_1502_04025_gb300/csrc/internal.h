@@ -314,6 +314,10 @@ std::unique_ptr<Workspace> make_workspace();
 size_t workspace_bytes(const Gauge *g, int m, int nrhs, qdd_prec sp, bool use_sap, int kdr = 0);
 size_t workspace_held(const Workspace *w);
 void workspace_release(Workspace *w);
+// every device allocation a solve with p makes: its workspace and the
+// precision copies of the gauge field it reads (the serving loop makes them
+// at admission, under its lock)
+qdd_status solve_prepare(Gauge *g, Workspace *w, const qdd_solve_params *p, cudaStream_t s);
 // rel_out (optional): true relative residual of every right-hand side at return
 qdd_status solve_impl(Gauge *g, Workspace *w, const double *b, double *x, int on_device,
                       const qdd_solve_params *p, qdd_report *rep, cudaStream_t s,

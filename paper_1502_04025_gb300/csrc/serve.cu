@@ -2,16 +2,18 @@
 // continuous batching.
 //
 // Requests queue on the context.  Worker threads (one CUDA stream and one
-// Krylov workspace each; max_slots of them) take the oldest request whose
-// workspace fits in the budget next to what is already resident, together
+// Krylov workspace each; max_slots of them) take the oldest request together
 // with every queued request for the same gauge field and parameters (up to
-// 12 right-hand sides), and solve them as one multi-right-hand-side batch:
+// 12 right-hand sides) once everything their solve allocates fits in the
+// budget next to what is already resident (allocated at admission, under
+// the queue lock), and solve them as one multi-right-hand-side batch:
 // one Schwarz launch per half-sweep covers all of them and reuses each staged
 // domain for every source.  Requests of different workers run concurrently
 // on the device.  Each right-hand side's arithmetic (Schwarz block solves,
 // operator, Gram-Schmidt, Givens) is independent of the others in the batch
 // and runs with the same launch shapes, so a result does not depend on the
 // mix it was solved in.
+#include <algorithm>
 #include <chrono>
 #include <cstring>
 
@@ -61,35 +63,52 @@ static void worker_main(Ctx *ctx)
                     return;
                 }
                 if (!ctx->queue.empty()) {
-                    // admission: the head request's workspace must fit next to
-                    // everything resident (this worker's own workspace is reused)
+                    // admission: the head request and every queued request for the
+                    // same gauge field and parameters (up to 12 right-hand sides)
+                    // form the batch.  Everything its solve allocates (workspace,
+                    // precision copies of the gauge field) is allocated here, under
+                    // the lock, so that admissions never count the same free memory
+                    // twice.  A batch that does not fit is retried with the head
+                    // alone, then waits for running solves to free memory; with
+                    // nothing running the head request is rejected.
                     auto head = ctx->queue.front();
-                    size_t need = workspace_bytes(head->g, head->p.restart_m, head->p.nrhs, head->p.sap_prec,
-                                                  head->p.use_sap != 0, head->p.dr_k);
-                    size_t held = workspace_held(ws.get());
-                    size_t used = ctx->used.load();
-                    size_t others = used > held ? used - held : 0;
-                    if (others + need <= ctx->budget) {
-                        int total = 0;
-                        for (auto it = ctx->queue.begin(); it != ctx->queue.end();) {
-                            auto &r = *it;
-                            bool take = batch.empty() ||
-                                        (r->g == head->g && same_params(r->p, head->p) &&
-                                         total + r->p.nrhs <= kMaxBatchRhs);
-                            if (take) {
-                                total += r->p.nrhs;
-                                batch.push_back(r);
-                                it = ctx->queue.erase(it);
-                            } else {
-                                ++it;
-                            }
+                    std::vector<std::shared_ptr<Request>> cand;
+                    int total = 0;
+                    for (auto &r : ctx->queue)
+                        if (cand.empty() || (r->g == head->g && same_params(r->p, head->p) &&
+                                             total + r->p.nrhs <= kMaxBatchRhs)) {
+                            cand.push_back(r);
+                            total += r->p.nrhs;
+                        }
+                    qdd_status ps = QDD_EBUDGET;
+                    for (int attempt = 0; attempt < 2 && ps == QDD_EBUDGET; attempt++) {
+                        if (attempt == 1) {
+                            if (cand.size() == 1) break;
+                            cand.resize(1);
+                            total = head->p.nrhs;
+                        }
+                        qdd_solve_params pm = head->p;
+                        pm.nrhs = total;
+                        size_t need = workspace_bytes(head->g, pm.restart_m, total, pm.sap_prec, pm.use_sap != 0,
+                                                      pm.dr_k);
+                        if (workspace_held(ws.get()) > 2 * need) workspace_release(ws.get());
+                        clear_error();
+                        ps = solve_prepare(head->g, ws.get(), &pm, st);
+                        if (ps == QDD_EBUDGET) workspace_release(ws.get());
+                    }
+                    if (ps == QDD_OK) {
+                        for (auto &r : cand) {
+                            batch.push_back(r);
+                            ctx->queue.erase(std::find(ctx->queue.begin(), ctx->queue.end(), r));
                         }
                         break;
                     }
-                    if (ctx->running == 0) {
-                        // nothing else can free memory: reject the head request
-                        head->status = QDD_EBUDGET;
-                        head->err = "request does not fit in the HBM budget";
+                    if (ps != QDD_EBUDGET || ctx->running == 0) {
+                        // an allocation failed for another reason, or nothing else
+                        // can free memory: reject the head request
+                        head->status = ps;
+                        head->err = ps == QDD_EBUDGET ? "request does not fit in the HBM budget"
+                                                      : std::string(qdd_last_error());
                         head->done = true;
                         ctx->queue.pop_front();
                         ctx->done_cv.notify_all();
@@ -119,8 +138,6 @@ static void worker_main(Ctx *ctx)
         pm.nrhs = total;
         qdd_report rep{};
         std::vector<double> rel;
-        size_t need = workspace_bytes(batch[0]->g, pm.restart_m, total, pm.sap_prec, pm.use_sap != 0, pm.dr_k);
-        if (workspace_held(ws.get()) > 2 * need) workspace_release(ws.get());
         clear_error();
         qdd_status s = single ? solve_impl(batch[0]->g, ws.get(), batch[0]->b.data(), batch[0]->x, 0, &pm, &rep, st,
                                            &rel)

@@ -123,6 +123,19 @@ static qdd_status ensure_ws(Gauge *g, Workspace &w, int m, int B, qdd_prec sp, b
     return QDD_OK;
 }
 
+qdd_status solve_prepare(Gauge *g, Workspace *w, const qdd_solve_params *p, cudaStream_t s)
+{
+    const qdd_prec sp = p->use_sap == 2 ? mg_smoother_prec(g) : p->sap_prec;
+    QDD_TRY(ensure_ws(g, *w, p->restart_m, p->nrhs, sp, p->use_sap == 1, p->dr_k));
+    if (p->use_sap) QDD_TRY(ensure_copy(g, sp, s));
+    if (p->arnoldi_prec != QDD_PREC_F64) QDD_TRY(ensure_copy(g, p->arnoldi_prec, s));
+    if (p->relax_eta > 0 || p->arnoldi_prec == QDD_PREC_F32) {
+        QDD_TRY(ensure_copy(g, QDD_PREC_F32, s));
+        if (g->two_rows) QDD_TRY(ensure_links12(g, QDD_PREC_F32, s));
+    }
+    return QDD_OK;
+}
+
 qdd_status solve_impl(Gauge *g, Workspace *wsp, const double *b_in, double *x_out, int on_device,
                       const qdd_solve_params *p, qdd_report *rep, cudaStream_t s, std::vector<double> *rel_out)
 {
@@ -157,10 +170,7 @@ qdd_status solve_impl(Gauge *g, Workspace *wsp, const double *b_in, double *x_ou
         return QDD_EINVAL;
     }
     Workspace &w = *wsp;
-    QDD_TRY(ensure_ws(g, w, m, B, sp, p->use_sap == 1, p->dr_k));
-    if (p->use_sap) QDD_TRY(ensure_copy(g, sp, s));
-    if (p->arnoldi_prec != QDD_PREC_F64) QDD_TRY(ensure_copy(g, p->arnoldi_prec, s));
-    if (p->relax_eta > 0) QDD_TRY(ensure_copy(g, QDD_PREC_F32, s));
+    QDD_TRY(solve_prepare(g, wsp, p, s));
     const int64_t n = (int64_t)g->hg.V * 12;
     const int64_t ldV = n * B;  // stride between basis vectors of one rhs
     double2 *V = w.V.as<double2>();
