@@ -181,7 +181,8 @@ class Clocks:
         os.unlink(self.f.name)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": sorted(reasons), "samples": len(sm),
-                "gpu_busy_fraction": statistics.mean(util) / 100 if util else None}
+                # meaningful only over several sample periods (the serving run)
+                "gpu_busy_fraction": statistics.mean(util) / 100 if len(util) >= 5 else None}
 
 
 def ncu_traffic(kernel):
