@@ -1,0 +1,35 @@
+"""The seeded gauge fields are SU(3) to rounding: U U^+ = 1 and det U = 1 for
+every link, eps = 0 gives unit links, and the third row of every link is the
+complex conjugate of the cross product of its first two (the identity the
+two-row operator copies rely on; it fails for a field that is not SU(3))."""
+import numpy as np
+
+from paper_1502_04025_gb300 import inputs
+
+
+def _third_row(U):
+    r0, r1 = U[..., 0, :], U[..., 1, :]
+    return np.conj(np.cross(r0, r1))
+
+
+def test_gauge_field_is_su3():
+    U = inputs.gauge_field((4, 4, 4, 6), 0.7, 1001).reshape(-1, 3, 3)
+    eye = np.eye(3)
+    dev = np.abs(U @ np.conj(np.swapaxes(U, -1, -2)) - eye).max()
+    assert dev <= 1e-13
+    assert np.abs(np.linalg.det(U) - 1.0).max() <= 1e-13
+    # a nontrivial field: far from the unit links
+    assert np.abs(U - eye).max() > 0.1
+
+
+def test_zero_eps_gives_unit_links():
+    U = inputs.gauge_field((4, 4, 4, 4), 0.0, 1002).reshape(-1, 3, 3)
+    assert np.abs(U - np.eye(3)).max() <= 1e-14  # W W^+ from the eigendecomposition, to rounding
+
+
+def test_third_row_is_the_conjugated_cross_product():
+    U = inputs.gauge_field((4, 4, 4, 4), 0.5, 1003)
+    assert np.abs(_third_row(U) - U[..., 2, :]).max() <= 1e-13
+    # a U(3) link with det != 1 breaks it
+    V = U * np.exp(0.3j)
+    assert np.abs(_third_row(V) - V[..., 2, :]).max() > 1e-2
