@@ -139,6 +139,28 @@ def test_links_that_are_not_su3_keep_three_rows(q, ctx, ora):
         q.qdd_destroy_gauge(g)
 
 
+@pytest.mark.parametrize("prec,half_ulp", [("f16", 2.0 ** -11), ("bf16", 2.0 ** -8)])
+def test_16bit_storage_round_trip_bound(q, ctx, prec, half_ulp):
+    """With kappa = 0 the operator is the identity (A = 1, hops scaled by 0), so a
+    16-bit apply returns its input rounded twice (stored with a per-site scale
+    = max |component|, round to nearest; then the output likewise): every
+    component lies within 2 half-ulps of the site's scale of the input."""
+    L, dom = (8, 8, 8, 8), (4, 4, 4, 4)
+    g = q.qdd_create_gauge_field(ctx, L, dom, inputs.gauge_field(L, 0.5, 1001))
+    try:
+        q.qdd_set_clover(g, 1.0, 0.0)
+        x = inputs.gaussian_source(L, 2031) * np.exp(inputs.gaussian_source(L, 2032).real)[..., :1, :1]
+        y = q.qdd_apply_D(g, x, prec)
+        scale = np.maximum(np.abs(x.real), np.abs(x.imag)).max(axis=(1, 2))
+        err = np.maximum(np.abs((y - x).real), np.abs((y - x).imag)).max(axis=(1, 2))
+        assert (err <= (2 * half_ulp + 1e-6) * scale).all()
+        assert (err > 0).any()  # the storage really is 16-bit
+        y64 = q.qdd_apply_D(g, x, "f64")
+        assert np.abs(y64 - x).max() <= 1e-15 * np.abs(x).max()
+    finally:
+        q.qdd_destroy_gauge(g)
+
+
 def test_dslash_multi_rhs(q, ctx, ora):
     P = problem(q, ctx, ora, (8, 8, 8, 8), (4, 4, 4, 4))
     xs = inputs.gaussian_source(P.L, 2002, nrhs=3)

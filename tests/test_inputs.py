@@ -33,3 +33,15 @@ def test_third_row_is_the_conjugated_cross_product():
     # a U(3) link with det != 1 breaks it
     V = U * np.exp(0.3j)
     assert np.abs(_third_row(V) - V[..., 2, :]).max() > 1e-2
+
+
+def test_sources():
+    L = (4, 4, 4, 4)
+    z = inputs.z2_source(L, 2005)
+    assert np.allclose(np.abs(z), 1.0, atol=1e-15)
+    assert set(np.round(z.ravel() * np.sqrt(2)).tolist()) == {1 + 1j, 1 - 1j, -1 + 1j, -1 - 1j}
+    P = inputs.point_sources(L, site=5).reshape(12, -1)
+    assert np.array_equal(np.abs(P).sum(1), np.ones(12))
+    assert np.array_equal(np.nonzero(P)[1], 5 * 12 + np.arange(12))  # site 5, spin*3 + colour in order
+    g = inputs.gaussian_source(L, 2001)
+    assert abs(g.real.std() - 1) < 0.05 and abs(g.imag.std() - 1) < 0.05
