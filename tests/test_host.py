@@ -42,6 +42,55 @@ def test_library_exports_every_declared_symbol(qdd):
     assert not missing, missing
 
 
+C_CLIENT = r"""
+#include <stdio.h>
+#include <stdlib.h>
+#include "qdd.h"
+int main(void)
+{
+    qdd_mg_params p;
+    qdd_mg_default_params(&p);
+    const int L[4] = {8, 8, 8, 8}, dom[4] = {4, 4, 4, 4};
+    int *site_of = malloc(4096 * sizeof(int));
+    uint16_t *nbl = malloc(256 * 8 * sizeof(uint16_t));
+    int *nbd = malloc(16 * 8 * sizeof(int));
+    qdd_status st = qdd_layout(L, dom, site_of, nbl, nbd);
+    const int bad[4] = {3, 8, 8, 8};
+    qdd_status st2 = qdd_layout(bad, dom, site_of, nbl, nbd);
+    unsigned long long hits = 1;
+    qdd_status st3 = qdd_check_hits(&hits);
+    printf("%d %d %.6f %d %d %d %llu\n", p.nv, p.bootstrap, qdd_load_model(8.0, 60.0), st, st2 == QDD_EINVAL,
+           st3 == QDD_EINVAL, hits);
+    free(site_of); free(nbl); free(nbd);
+    return 0;
+}
+"""
+
+
+def test_plain_c_client_links_and_calls_host_entry_points(qdd, tmp_path):
+    """The header is plain C (C99, -pedantic) and a C program links against
+    libqdd.so and calls its host-only entry points (no GPU needed)."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "client.c"
+    src.write_text(C_CLIENT)
+    exe = tmp_path / "client"
+    libdir = os.path.dirname(qdd.LIB_PATH)
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        str(src), "-o", str(exe), "-L", libdir, "-l:" + os.path.basename(qdd.LIB_PATH),
+                        "-Wl,-rpath," + libdir], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0, out.stderr
+    nv, boot, load, st, bad, nocheck, hits = out.stdout.split()
+    assert (nv, boot, st, bad, nocheck, hits) == ("8", "0", "0", "1", "1", "0")
+    assert abs(float(load) - qdd.qdd_load_model(8.0, 60.0)) < 1e-6
+
+
 def test_binding_covers_every_symbol(qdd):
     for n in declared_functions():
         assert hasattr(qdd, n), n
