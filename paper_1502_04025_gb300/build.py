@@ -41,7 +41,7 @@ def _stale(obj: str, src: str) -> bool:
         return True
     t = os.path.getmtime(obj)
     deps = [src, os.path.join(CSRC, "common.cuh"), os.path.join(CSRC, "internal.h"),
-            os.path.join(ROOT, "include", "qdd.h")]
+            os.path.join(CSRC, "admission.h"), os.path.join(ROOT, "include", "qdd.h")]
     return any(os.path.getmtime(d) > t for d in deps)
 
 

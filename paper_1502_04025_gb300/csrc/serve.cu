@@ -17,6 +17,7 @@
 #include <chrono>
 #include <cstring>
 
+#include "admission.h"
 #include "internal.h"
 
 namespace qdd {
@@ -69,74 +70,39 @@ static void worker_main(Ctx *ctx)
                     return;
                 }
                 if (!ctx->queue.empty()) {
-                    // admission: a lead request and every queued request for the
-                    // same gauge field and parameters (up to 12 right-hand sides)
-                    // form the batch.  Everything its solve allocates (workspace,
-                    // precision copies of the gauge field) is allocated here, under
-                    // the lock, so that admissions never count the same free memory
-                    // twice.  A batch that does not fit is retried with its lead
-                    // alone.  The lead is the head of the queue; while the head does
-                    // not fit, later requests that fit may go first (at most
-                    // kMaxBypass of them), so that a large request does not block
-                    // small ones behind it.  With nothing running, a head that does
-                    // not fit is rejected.
-                    auto head = ctx->queue.front();
-                    const int nlead = head->bypassed < kMaxBypass ? (int)ctx->queue.size() : 1;
-                    qdd_status ps = QDD_EBUDGET;
-                    std::vector<std::shared_ptr<Request>> cand;
-                    std::shared_ptr<Request> lead;
-                    for (int li = 0; li < nlead && ps == QDD_EBUDGET; li++) {
-                        lead = ctx->queue[li];
-                        cand.clear();
-                        int total = 0;
-                        cand.push_back(lead);
-                        total = lead->p.nrhs;
-                        for (auto &r : ctx->queue)
-                            if (r != lead && r->g == lead->g && same_params(r->p, lead->p) &&
-                                total + r->p.nrhs <= kMaxBatchRhs) {
-                                cand.push_back(r);
-                                total += r->p.nrhs;
-                            }
-                        for (int attempt = 0; attempt < 2 && ps == QDD_EBUDGET; attempt++) {
-                            if (attempt == 1) {
-                                if (cand.size() == 1) break;
-                                cand.resize(1);
-                                total = lead->p.nrhs;
-                            }
-                            qdd_solve_params pm = lead->p;
-                            pm.nrhs = total;
-                            size_t need = workspace_bytes(lead->g, pm.restart_m, total, pm.sap_prec, pm.use_sap != 0,
-                                                          pm.dr_k);
-                            // a workspace that cannot fit next to everything else is not tried
-                            const size_t held = workspace_held(ws.get()), used = ctx->used.load();
-                            if ((used > held ? used - held : 0) + need > ctx->budget) {
-                                ps = QDD_EBUDGET;
-                                continue;
-                            }
-                            if (held > 2 * need) workspace_release(ws.get());
-                            clear_error();
-                            ps = solve_prepare(lead->g, ws.get(), &pm, st);
-                            if (ps == QDD_EBUDGET) workspace_release(ws.get());
-                        }
-                        if (ps != QDD_OK && ps != QDD_EBUDGET) break;  // a real error: reported below
-                    }
-                    if (ps == QDD_OK) {
-                        if (std::find(cand.begin(), cand.end(), head) == cand.end()) head->bypassed++;
-                        for (auto &r : cand) {
-                            batch.push_back(r);
-                            ctx->queue.erase(std::find(ctx->queue.begin(), ctx->queue.end(), r));
-                        }
+                    // admission (the rules: admission.h).  Everything a batch's solve
+                    // allocates (workspace, precision copies of the gauge field) is
+                    // allocated here, under the lock, so that admissions never count
+                    // the same free memory twice.
+                    auto prepare = [&](const Request &lead, int total) -> qdd_status {
+                        qdd_solve_params pm = lead.p;
+                        pm.nrhs = total;
+                        const size_t need = workspace_bytes(lead.g, pm.restart_m, total, pm.sap_prec,
+                                                            pm.use_sap != 0, pm.dr_k);
+                        // a workspace that cannot fit next to everything else is not tried
+                        const size_t held = workspace_held(ws.get()), used = ctx->used.load();
+                        if ((used > held ? used - held : 0) + need > ctx->budget) return QDD_EBUDGET;
+                        if (held > 2 * need) workspace_release(ws.get());
+                        clear_error();
+                        qdd_status ps = solve_prepare(lead.g, ws.get(), &pm, st);
+                        if (ps == QDD_EBUDGET) workspace_release(ws.get());
+                        return ps;
+                    };
+                    auto res = admit(
+                        ctx->queue, ctx->running > 0, kMaxBatchRhs, kMaxBypass,
+                        [](const Request &r) { return r.p.nrhs; },
+                        [](const Request &a, const Request &b) { return a.g == b.g && same_params(a.p, b.p); },
+                        prepare);
+                    if (res.what == Admit::kBatch) {
+                        batch = std::move(res.batch);
                         break;
                     }
-                    if (ps != QDD_EBUDGET || ctx->running == 0) {
-                        // an allocation failed for another reason (that lead request
-                        // fails), or nothing else can free memory (the head fails)
-                        auto bad = ps != QDD_EBUDGET ? lead : head;
-                        bad->status = ps;
-                        bad->err = ps == QDD_EBUDGET ? "request does not fit in the HBM budget"
-                                                     : std::string(qdd_last_error());
+                    if (res.what == Admit::kReject) {
+                        auto &bad = res.rejected;
+                        bad->status = res.status;
+                        bad->err = res.status == QDD_EBUDGET ? "request does not fit in the HBM budget"
+                                                             : std::string(qdd_last_error());
                         bad->done = true;
-                        ctx->queue.erase(std::find(ctx->queue.begin(), ctx->queue.end(), bad));
                         ctx->done_cv.notify_all();
                         continue;
                     }

@@ -179,3 +179,98 @@ def test_layout_rejects_bad_geometry(qdd):
         qdd.qdd_layout((8, 8, 8, 8), (3, 4, 4, 4))   # odd extent
     with pytest.raises(qdd.QddError):
         qdd.qdd_layout((32, 16, 16, 16), (16, 8, 4, 4))  # domain above 512 sites
+
+
+ADMIT_DRIVER = r"""
+#include <cstdio>
+#include "admission.h"
+using namespace qdd;
+struct R { int id, g, nrhs; long bytes; int bypassed; };
+static std::shared_ptr<R> req(int id, int g, int nrhs, long bytes) { return std::make_shared<R>(R{id, g, nrhs, bytes, 0}); }
+static void show(const char *name, const AdmitResult<R> &res, const std::deque<std::shared_ptr<R>> &q)
+{
+    std::printf("%s %s", name, res.what == Admit::kBatch ? "batch" : res.what == Admit::kWait ? "wait" : "reject");
+    for (auto &r : res.batch) std::printf(" %d", r->id);
+    if (res.rejected) std::printf(" rejected=%d status=%d", res.rejected->id, (int)res.status);
+    std::printf(" | left");
+    for (auto &r : q) std::printf(" %d", r->id);
+    std::printf("\n");
+}
+int main()
+{
+    long budget = 0;
+    int err_id = -1;
+    auto nrhs = [](const R &r) { return r.nrhs; };
+    auto same = [](const R &a, const R &b) { return a.g == b.g; };
+    auto prepare = [&](const R &lead, int total) {
+        if (lead.id == err_id) return QDD_ENOMEM;
+        return lead.bytes * total <= budget ? QDD_OK : QDD_EBUDGET;
+    };
+    {   // same gauge merges up to 12 right-hand sides, in queue order
+        std::deque<std::shared_ptr<R>> q{req(0, 1, 4, 1), req(1, 2, 4, 1), req(2, 1, 4, 1), req(3, 1, 6, 1)};
+        budget = 100;
+        auto res = admit(q, true, 12, 8, nrhs, same, prepare);
+        show("merge", res, q);
+    }
+    {   // the merged batch does not fit, its lead alone does
+        std::deque<std::shared_ptr<R>> q{req(0, 1, 6, 10), req(1, 1, 6, 10)};
+        budget = 60;
+        auto res = admit(q, true, 12, 8, nrhs, same, prepare);
+        show("shrink", res, q);
+    }
+    {   // a head that does not fit lets a later request that fits go first
+        std::deque<std::shared_ptr<R>> q{req(0, 1, 1, 100), req(1, 2, 1, 10), req(2, 3, 1, 10)};
+        budget = 50;
+        auto res = admit(q, true, 12, 8, nrhs, same, prepare);
+        show("bypass", res, q);
+        std::printf("bypassed %d\n", q.front()->bypassed);
+        q.front()->bypassed = 8;  // the bound reached: wait for the head
+        auto res2 = admit(q, true, 12, 8, nrhs, same, prepare);
+        show("bound", res2, q);
+    }
+    {   // nothing running: a head that does not fit is rejected
+        std::deque<std::shared_ptr<R>> q{req(0, 1, 1, 100), req(1, 2, 1, 100)};
+        budget = 50;
+        auto res = admit(q, false, 12, 8, nrhs, same, prepare);
+        show("reject", res, q);
+    }
+    {   // another preparation error fails the request it belongs to
+        std::deque<std::shared_ptr<R>> q{req(0, 1, 1, 100), req(1, 2, 1, 10)};
+        budget = 50;
+        err_id = 1;
+        auto res = admit(q, true, 12, 8, nrhs, same, prepare);
+        show("error", res, q);
+    }
+    return 0;
+}
+"""
+
+
+def test_serving_admission_policy(tmp_path):
+    """The serving loop's admission rules (csrc/admission.h), compiled on the
+    host with a fake memory budget: batching, shrinking to the lead, bounded
+    bypass of a head that does not fit, rejection with nothing running, and
+    error attribution."""
+    import shutil
+    import subprocess
+
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no C++ compiler")
+    src = tmp_path / "admit.cpp"
+    src.write_text(ADMIT_DRIVER)
+    exe = tmp_path / "admit"
+    r = subprocess.run([cxx, "-std=c++17", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        "-I", os.path.join(ROOT, "paper_1502_04025_gb300", "csrc"), str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60).stdout.splitlines()
+    assert out == [
+        "merge batch 0 2 | left 1 3",
+        "shrink batch 0 | left 1",
+        "bypass batch 1 | left 0 2",
+        "bypassed 1",
+        "bound wait | left 0 2",
+        "reject reject rejected=0 status=3 | left 1",
+        "error reject rejected=1 status=2 | left 0",
+    ], out
