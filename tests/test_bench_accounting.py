@@ -1,0 +1,62 @@
+"""The bench's roofline accounting on the host: hops that leave a domain
+(against a brute-force count over the domain's sites), the Schwarz flop
+count per site, the operator's algorithmic bytes per site, and the DRAM
+traffic record, which is reported only while the kernel's sources match."""
+import itertools
+import json
+import os
+import shutil
+
+import pytest
+
+import bench
+
+
+def _leaving_hops_brute(dom):
+    total = 0
+    for c in itertools.product(*[range(d) for d in dom]):
+        for mu in range(4):
+            total += (c[mu] + 1 >= dom[mu]) + (c[mu] - 1 < 0)
+    return total / float(dom[0] * dom[1] * dom[2] * dom[3])
+
+
+@pytest.mark.parametrize("dom", [(8, 4, 4, 4), (4, 4, 4, 4), (2, 2, 2, 2), (6, 4, 2, 2)])
+def test_crossing_hops_per_site(dom):
+    assert bench.crossing_hops_per_site(dom) == pytest.approx(_leaving_hops_brute(dom), rel=1e-15)
+
+
+def test_sap_flop_per_site():
+    # per even/odd pair: setup (clover + hops + combine on the odd site's reconstruction input), nmr MR
+    # steps of two full applies plus the MR vector algebra, and the final reconstruction; then
+    # the entering hops of the inflow
+    full = 1320 + 504 + 24
+    pair = full + 4 * (2 * full + 336) + full
+    assert bench.sap_flop_per_site((8, 4, 4, 4), 4) == pytest.approx(pair / 2 + 1.75 * 168)
+    assert bench.sap_flop_per_site((8, 4, 4, 4), 4) == pytest.approx(10206.0)
+    # one launch sweeps half the sites: the 16^3x32 workload's flop per launch
+    assert 16 * 16 * 16 * 32 // 2 * bench.sap_flop_per_site((8, 4, 4, 4), 4) == pytest.approx(668860416.0)
+
+
+def test_operator_bytes_per_site():
+    got = {p: (bench.op_bytes_per_site(p, True), bench.op_bytes_per_site(p, False))
+           for p in ("f64", "df64", "f32", "h16", "f16", "bf16")}
+    assert got == {"f64": (1536, 1536), "df64": (1536, 1536), "f32": (768, 672), "h16": (484, 436),
+                   "f16": (396, 348), "bf16": (396, 348)}
+
+
+def test_traffic_record_only_while_sources_match(tmp_path, monkeypatch):
+    rec = json.load(open(os.path.join(bench.ROOT, "profiles", "traffic.json")))["k_sap"]
+    assert bench.ncu_traffic("k_sap") == rec["dram_bytes_per_launch"]
+    # a copy of the tree whose kernel source differs by one byte
+    (tmp_path / "profiles").mkdir()
+    shutil.copy(os.path.join(bench.ROOT, "profiles", "traffic.json"), tmp_path / "profiles" / "traffic.json")
+    for src in rec["sources"]:
+        dst = tmp_path / src
+        dst.parent.mkdir(parents=True, exist_ok=True)
+        shutil.copy(os.path.join(bench.ROOT, src), dst)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.ncu_traffic("k_sap") == rec["dram_bytes_per_launch"]
+    with open(tmp_path / rec["sources"][0], "a") as f:
+        f.write("\n")
+    assert bench.ncu_traffic("k_sap") is None
+    assert bench.ncu_traffic("no_such_kernel") is None
