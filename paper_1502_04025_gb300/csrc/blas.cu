@@ -3,11 +3,13 @@
 // basis updates and the solution update run in FP64 on the device.
 //
 // Vectors are flat arrays of complex FP64 (double2); the lattice layout does
-// not matter here.  All reductions are two-pass and deterministic: a fixed
-// number of blocks (a multiple of the SM count) writes per-block partials in a
-// fixed order, one block sums them in a fixed order.  Fused forms read each
-// vector once: the multi-dot reads w once for all basis vectors, the
-// multi-axpy writes w once and returns its new norm.
+// not matter here.  All reductions are two-level and deterministic: a fixed
+// number of blocks (a multiple of the SM count) writes per-block partials,
+// and the last block to finish (a counter in the scratch buffer) sums them in
+// block order; the allocation-free entry point sums them in a separate
+// launch instead.  Fused forms read each vector once: the multi-dot reads w
+// once for all basis vectors, the multi-axpy writes w once and returns its
+// new norm.
 #include <mutex>
 #include <type_traits>
 
