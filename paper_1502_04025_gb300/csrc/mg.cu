@@ -15,12 +15,17 @@
 //   V-cycle     e_c ~ D_c^{-1} P^H v by one GMRES cycle of coarse_iters steps
 //               from zero, z = P e_c, r = v - D z, z += M_SAP(r) (post_ncy
 //               cycles)
+//   bootstrap   (the adaptive setup, `bootstrap` passes) each w_k becomes the
+//               V-cycle of the method built so far applied to column k of P,
+//               normalised; P and D_c are rebuilt from them
 //
 // The coarse problem is small (2 nv unknowns per domain), so its GMRES cycle
-// runs without the host: per step one multi-CTA stencil launch and one
-// single-CTA launch that does the Gram-Schmidt dots, the update, the norm, the
-// complex Givens rotation and the normalisation; the least-squares solution is
-// a back substitution at the end.
+// runs without the host, captured once into a CUDA graph: per step one
+// stencil launch (a CTA per domain) and one launch of an 8-CTA thread-block
+// cluster that does the Gram-Schmidt dots, the update, the norm, the complex
+// Givens rotation and the normalisation, its CTAs owning slices of the basis
+// and exchanging partial sums through distributed shared memory; the
+// least-squares solution is a back substitution at the end.
 //
 // Layouts: P as nv fine fields in the domain-blocked layout, so that the
 // block (a, chi) of column k is the contiguous run of planes 6 chi .. 6 chi + 5
