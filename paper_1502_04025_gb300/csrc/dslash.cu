@@ -12,7 +12,10 @@
 // the hop leaves the domain) and a per-domain table of neighbouring domains.
 // The roofline of this kernel is HBM bandwidth: each link, clover entry and
 // input spinor is read once and the output written once when the neighbour
-// re-reads hit in L1/L2.
+// re-reads hit in L1/L2.  For SU(3) fields the FP32 and 16-bit forms read
+// only the first two rows of each link and rebuild the third (96 fewer bytes
+// per site in FP32), and their 16-bit link and clover copies are stored with
+// planes paired, one 8-byte load per two planes.
 #include "internal.h"
 
 namespace qdd {
