@@ -25,6 +25,22 @@ def test_crossing_hops_per_site(dom):
     assert bench.crossing_hops_per_site(dom) == pytest.approx(_leaving_hops_brute(dom), rel=1e-15)
 
 
+def test_operator_flop_decomposition():
+    """Sec. 3.7 prints 1848 flop/site for Wilson-clover; the bench's count is
+    hops 1320 + two Hermitian 6x6 clover blocks 504 + the final combination 24
+    (tests/golden/paper_values.json)."""
+    golden = json.load(open(os.path.join(bench.ROOT, "tests", "golden", "paper_values.json")))
+    f = bench.SAP_FLOP
+    assert f["hop"] + f["clover"] + f["combine"] == golden["flops_per_site"]["wilson_clover"]
+    # eight spin-projected hops: per hop the projection (6 complex adds, 12 flop) and two 3x3 complex
+    # matrix-vector products (9 complex multiplies at 6 and 6 complex adds at 2: 66 each); the 12
+    # complex components of the 8 results are summed with 7 adds each (24 flop per add of a spinor)
+    assert 8 * (12 + 2 * 66) + 7 * 24 == f["hop"]
+    # a Hermitian 6x6 block times a complex 6-vector: 6 real diagonal entries times complex (12), the
+    # 15 off-diagonal entries used twice (30 complex multiplies, 180), 5 complex adds per row (60)
+    assert 2 * (12 + 30 * 6 + 6 * 5 * 2) == f["clover"]
+
+
 def test_sap_flop_per_site():
     # per even/odd pair: setup (clover + hops + combine on the odd site's reconstruction input), nmr MR
     # steps of two full applies plus the MR vector algebra, and the final reconstruction; then

@@ -2,6 +2,7 @@
 every entry point its header declares, and the pure host functions match
 the numbers the paper prints."""
 import ctypes
+import json
 import os
 import re
 
@@ -96,16 +97,20 @@ def test_binding_covers_every_symbol(qdd):
         assert hasattr(qdd, n), n
 
 
+GOLDEN = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_values.json")))
+
+
 def test_load_model_pins(qdd):
     """Sec. 3.5: 64^3x128 on 1024 KNCs with 8x4^3 domains gives N_d = 64
     domains per KNC and 60 usable cores, load x/ceil(x) = 53%; the
-    non-uniform split 128 = 4*28+16 gives (4*56+32)/(5*60) = 85%."""
-    assert qdd.qdd_load_model(64 / 2, 60) == pytest.approx(32 / 60)
-    assert round(100 * qdd.qdd_load_model(32, 60)) == 53
+    non-uniform split 128 = 4*28+16 gives (4*56+32)/(5*60) = 85%
+    (tests/golden/paper_values.json)."""
+    u, nu = GOLDEN["load_model"]["uniform"], GOLDEN["load_model"]["non_uniform"]
+    assert qdd.qdd_load_model(u["domains_per_colour"], u["slots"]) == pytest.approx(32 / 60)
+    assert round(100 * qdd.qdd_load_model(u["domains_per_colour"], u["slots"])) == u["load_percent"]
     # t-slices of 28 and 16 sites hold 56 and 32 domains per colour pair
-    loads = [qdd.qdd_load_model(n / 2, 60) * 1 for n in (56 * 2, 56 * 2, 56 * 2, 56 * 2, 32 * 2)]
-    per_knc_busy = [56, 56, 56, 56, 32]
-    assert round(100 * sum(per_knc_busy) / (5 * 60)) == 85
+    loads = [qdd.qdd_load_model(n, nu["slots"]) for n in nu["busy_per_knc"]]
+    assert round(100 * sum(nu["busy_per_knc"]) / (len(nu["busy_per_knc"]) * nu["slots"])) == nu["load_percent"]
     assert all(0 < l <= 1 for l in loads)
     assert qdd.qdd_load_model(120, 60) == 1.0
     assert qdd.qdd_load_model(0, 60) == 0.0
@@ -114,10 +119,11 @@ def test_load_model_pins(qdd):
 def test_working_set_pins(qdd):
     """Sec. 3.3: an 8x4^3 domain needs 456 kB in single precision and 312 kB
     with half-precision links and clover (two full spinors plus three
-    even-site spinors of the MR iteration)."""
-    dom = (8, 4, 4, 4)
-    assert qdd.qdd_domain_working_set(dom, 4, 2, 3) == 456 * 1024
-    assert qdd.qdd_domain_working_set(dom, 2, 2, 3) == 312 * 1024
+    even-site spinors of the MR iteration; tests/golden/paper_values.json)."""
+    w = GOLDEN["working_set"]
+    dom = tuple(w["domain"])
+    assert qdd.qdd_domain_working_set(dom, 4, 2, 3) == w["single_precision_kB"] * 1024
+    assert qdd.qdd_domain_working_set(dom, 2, 2, 3) == w["half_links_clover_kB"] * 1024
 
 
 def test_no_gpu_needed_for_errors(qdd):
