@@ -280,3 +280,16 @@ def test_serving_admission_policy(tmp_path):
         "reject reject rejected=0 status=3 | left 1",
         "error reject rejected=1 status=2 | left 0",
     ], out
+
+
+def test_multigrid_parameters_binding(qdd):
+    """The C defaults reach Python field by field (no GPU involved), keyword
+    overrides land in the struct, and a misspelt keyword is an error rather
+    than a silently ignored attribute."""
+    p = qdd.qdd_mg_default_params()
+    assert (p.nv, p.setup_iters, p.setup_ncy, p.nmr, p.post_ncy, p.coarse_iters, p.sap_prec, p.bootstrap) == \
+        (8, 3, 2, 4, 2, 12, qdd.QDD_PREC_F32, 0)
+    p = qdd.qdd_mg_default_params(nv=12, bootstrap=2, sap_prec="f64")
+    assert (p.nv, p.bootstrap, p.sap_prec) == (12, 2, qdd.QDD_PREC_F64)
+    with pytest.raises(TypeError):
+        qdd.qdd_mg_default_params(boot_strap=1)
