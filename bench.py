@@ -2,21 +2,25 @@
 """Benchmark: SAP-preconditioned FGMRES time-to-solution for the
 Wilson-clover Dirac equation on one GB300 (arXiv:1502.04025, Sec. 3).
 
-Workload (one step = one complete solve to a true FP64 relative residual of
-1e-10): 16^3x32 lattice, seeded SU(3) links U = exp(i 0.5 H), c_sw 1.0,
-kappa 0.125, 8x4x4x4 domains, FP32 Schwarz preconditioner (nmr 4, ncy 4) on
-FP32 storage, FP64 FGMRES(16), one Gaussian source.  Inputs are resident in
-HBM when the timed region starts; L2 is flushed (256 MB write) before every
-step.  The same solve through the C ABI with host buffers gives "e2e".
+Default workload (one step = one complete solve to a true FP64 relative
+residual of 1e-10): the largest single-GPU configuration, 48^3x96 lattice
+(10.6 million sites), seeded SU(3) links U = exp(i 0.7 H), c_sw 1.5,
+kappa 0.1355, 4^4 domains, Schwarz preconditioner (nmr 4, ncy 4) in FP32
+arithmetic on BF16 storage, FP64 FGMRES(16) (the Krylov basis alone is
+34 GB), one Z2 noise source.  Inputs are resident in HBM when the timed
+region starts; the working set is far larger than L2 and a 256 MB buffer is
+written before every step as well.  The same solve through the C ABI with
+host buffers gives "e2e".  --config 1..3 select the other configurations.
 
 --impl reference times the FP64 CPU reference checker (oracle/) on a bounded
-sample of the same workload (one FGMRES iteration per step) and scales it to
-a time-to-solution with the iteration count the checker needs on this
-workload (oracle/iterations_16c32.json, written by oracle/measure_iterations.py).
+sample of the same workload: the oracle's operator at sampled sites of the
+same gauge field and source, one sample per step; the line's value is that
+measured time.  Time-to-solution estimates scaled from the sample are in
+separately named keys.
 
 Under torchrun (--gpus N) every rank solves its own copy of the workload
-(replicas; the solver has no multi-GPU path), the timed region is bracketed
-by barriers, and the slowest rank's time is reported.
+(replicas), the timed region is bracketed by barriers, and the slowest
+rank's time is reported.
 """
 from __future__ import annotations
 
@@ -39,20 +43,25 @@ WL = dict(L=(16, 16, 16, 32), dom=(8, 4, 4, 4), eps=0.5, csw=1.0, kappa=0.125, g
 # full-lattice operator throughput: a lattice larger than L2 (32^3x64, eps 0.7, c_sw 1.5, kappa 0.1355)
 DSL = dict(L=(32, 32, 32, 64), dom=(4, 4, 4, 4), eps=0.7, csw=1.5, kappa=0.1355, gauge_seed=1003, source_seed=2003)
 METRIC = "SAP-FGMRES time-to-1e-10 residual"
-WORKLOAD_NAME = ("16^3x32 Wilson-clover, c_sw 1.0, kappa 0.125, eps 0.5 links; SAP-FGMRES(16), 8x4x4x4 domains, "
-                 "nmr 4, ncy 4, FP32 preconditioner, FP64 outer (Gram-Schmidt, least squares, solution, true "
-                 "residual; double-float Arnoldi operator relaxed to FP32 below est 1e-5), tol 1e-10, "
-                 "1 Gaussian source")
-SAP_FLOP = {"hop": 1320, "clover": 504, "combine": 24, "mr_blas": 336, "boundary_hop": 168}
+# flop of the operator's parts: all eight hops of a site (1320 = 8 hops of 144, summed with 7 spinor adds of
+# 24), two Hermitian 6x6 clover blocks, the final combination; MR vector algebra per even site; one hop entering
+# a domain across its boundary (hop and its add)
+SAP_FLOP = {"hop": 1320, "hop_one": 144, "spinor_add": 24, "clover": 504, "combine": 24, "mr_blas": 336,
+            "boundary_hop": 168}
 L2_FLUSH_BYTES = 256 << 20
+DEFAULT_CONFIG = 4
 
 
-# the other workload configurations (run with --config N; the default line is configuration 2)
+# the workload configurations (--config N; the default line is the largest single-GPU one, 4)
 CONFIGS = {
     1: dict(L=(8, 8, 8, 8), dom=(4, 4, 4, 4), eps=0.5, csw=1.0, kappa=0.12, gauge_seed=1001, source_seed=2001,
             nmr=4, ncy=4, m=16, tol=1e-10, sap_prec="f64", arnoldi_prec="f64", source="gaussian", nrhs=1,
             name="8^4 plain FP64 SAP-FGMRES(16), 4^4 domains, c_sw 1.0, kappa 0.12, eps 0.5"),
-    2: dict(WL, source="gaussian", nrhs=1, name=WORKLOAD_NAME),
+    2: dict(WL, source="gaussian", nrhs=1,
+            name=("16^3x32 Wilson-clover, c_sw 1.0, kappa 0.125, eps 0.5 links; SAP-FGMRES(16), 8x4x4x4 domains, "
+                  "nmr 4, ncy 4, FP32 preconditioner, FP64 outer (Gram-Schmidt, least squares, solution, true "
+                  "residual; double-float Arnoldi operator relaxed to FP32 below est 1e-5), tol 1e-10, "
+                  "1 Gaussian source")),
     3: dict(L=(32, 32, 32, 64), dom=(4, 4, 4, 4), eps=0.7, csw=1.5, kappa=0.1355, gauge_seed=1003, source_seed=2003,
             nmr=4, ncy=4, m=16, tol=1e-10, sap_prec="f16", arnoldi_prec="df64", relax_eta=1e-6, reorth=0,
             source="point12", nrhs=12,
@@ -60,15 +69,18 @@ CONFIGS = {
     4: dict(L=(48, 48, 48, 96), dom=(4, 4, 4, 4), eps=0.7, csw=1.5, kappa=0.1355, gauge_seed=1004, source_seed=2004,
             nmr=4, ncy=4, m=16, tol=1e-10, sap_prec="bf16", arnoldi_prec="df64", relax_eta=1e-6, reorth=0,
             source="z2", nrhs=1,
-            name="48^3x96, eps 0.7, c_sw 1.5, kappa 0.1355, BF16-stored SAP, FP64 FGMRES(16), Z2 source"),
+            name=("48^3x96 (10,616,832 sites), eps 0.7, c_sw 1.5, kappa 0.1355, 4^4 domains, nmr 4, ncy 4, "
+                  "BF16-stored Schwarz preconditioner with FP32 arithmetic, FP64 FGMRES(16) (Gram-Schmidt, least "
+                  "squares, solution, true residual; double-float Arnoldi operator relaxed to FP32 below est "
+                  "1e-5), tol 1e-10, one Z2 noise source")),
 }
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4],
-                    help="workload configuration (2 = the default benchmark line)")
+    ap.add_argument("--config", type=int, default=DEFAULT_CONFIG, choices=[1, 2, 3, 4],
+                    help="workload configuration (4, the largest single-GPU one, is the default line)")
     ap.add_argument("--serve", action="store_true", help="run the serving mix instead of single solves")
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--op-bench", action="store_true", help="time only the full-lattice operator")
@@ -119,16 +131,20 @@ def crossing_hops_per_site(dom):
 
 def sap_flop_per_site(dom, nmr):
     """Algorithmic FP32 flop per site of one domain visit of the Schwarz
-    kernel, counted as for the operator (1848 per full site apply):
-      setup   t_o = A^-1 rho_o (504 per odd site), bhat_e (hops + combine per even site)
-      MR      per step: odd site t = A^-1(-k H r) 1848, even site p = A r + k H t 1848,
-              dots and updates 336 per even site
-      recon   odd site x_o = A^-1(rho_o + k H x_e) 1848
-      inflow  168 per hop entering from a neighbouring domain."""
+    kernel.  Inside the domain the operator has only the hops that stay in
+    it (Dirichlet boundary): 8 - c per site on average, c the hops that leave
+    (crossing_hops_per_site), each 144 flop, summed with 7 - c spinor adds:
+      setup   t_o = A^-1 rho_o (504 per odd site), bhat_e (inner hops + combine per even site)
+      MR      per step: odd site t = A^-1(-k H r), even site p = A r + k H t (inner hops + clover +
+              combine each), dots and updates 336 per even site
+      recon   odd site x_o = A^-1(rho_o + k H x_e)
+      inflow  168 per hop entering from a neighbouring domain (c per site)."""
     f = SAP_FLOP
-    full = f["hop"] + f["clover"] + f["combine"]
-    per_pair = (f["clover"] + f["hop"] + f["combine"]) + nmr * (2 * full + f["mr_blas"]) + full
-    return per_pair / 2 + crossing_hops_per_site(dom) * f["boundary_hop"]
+    c = crossing_hops_per_site(dom)
+    hops = (8 - c) * f["hop_one"] + (7 - c) * f["spinor_add"]
+    full = hops + f["clover"] + f["combine"]
+    per_pair = (f["clover"] + hops + f["combine"]) + nmr * (2 * full + f["mr_blas"]) + full
+    return per_pair / 2 + c * f["boundary_hop"]
 
 
 # ------------------------------------------------------------------ clocks
@@ -205,33 +221,92 @@ def ncu_traffic(kernel):
 
 # --------------------------------------------------------------- oracle leg
 
-def oracle_sample(w, U=None):
-    """Time a bounded sample of the FP64 oracle on the workload: FGMRES with
-    one and with two Arnoldi steps, giving the cost per step and the fixed
-    cost; scaled to a solve with the oracle's own iteration count."""
+def host_info():
+    """Host cores and CPU model of the machine the oracle runs on."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu part", "hardware") and model is None:
+                    model = line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+
+    return {"nproc": os.cpu_count(), "cpu": model, "machine": platform.machine()}
+
+
+def oracle_cost_units(W):
+    """The oracle's cost of one FGMRES iteration and of the fixed part of a
+    solve (two true residuals), in units of its operator evaluated at every
+    site through apply_D_sites, measured on a small lattice (two domains per
+    direction) with the workload's parameters."""
     from oracle import pyoracle as ora
     from paper_1502_04025_gb300 import inputs
 
-    with open(os.path.join(ROOT, "oracle", "iterations_16c32.json")) as f:
-        it = json.load(f)
-    if U is None:
-        U = inputs.gauge_field(w["L"], w["eps"], w["gauge_seed"])
-    b = inputs.gaussian_source(w["L"], w["source_seed"])
-    A = ora.clover(w["L"], U, w["csw"], w["kappa"])
-    Ainv = ora.invert_clover(w["L"], A)
-    times = []
-    for m in (1, 2):
-        t0 = time.perf_counter()
-        ora.fgmres(w["L"], w["dom"], U, A, Ainv, w["kappa"], b, 1e-30, m=m, max_restarts=0, use_sap=True,
-                   nmr=w["nmr"], ncy=w["ncy"])
-        times.append(time.perf_counter() - t0)
-    per_iter = max(times[1] - times[0], 0.0)
-    fixed = max(times[0] - per_iter, 0.0)  # initial and final residual (two operator applies)
-    est_s = fixed * (1 + it["restarts"]) + per_iter * it["iterations"]
-    return {"value": est_s * 1e3, "unit": "ms", "cores": 1, "kind": "oracle",
-            "sample": (f"FP64 oracle FGMRES with 1 and 2 Arnoldi steps on the full 16^3x32 workload "
-                       f"({times[0]:.1f} s, {times[1]:.1f} s), scaled to its {it['iterations']} iterations and "
-                       f"{it['restarts']} restarts to 1e-10")}
+    Ls = tuple(2 * d for d in W["dom"])
+    Us = inputs.gauge_field(Ls, W["eps"], W["gauge_seed"])
+    bs = inputs.gaussian_source(Ls, W["source_seed"])
+    As = ora.clover(Ls, Us, W["csw"], W["kappa"])
+    Ais = ora.invert_clover(Ls, As)
+    Vs = int(np.prod(Ls))
+
+    def best(fn, k=2):
+        t = []
+        for _ in range(k):
+            t0 = time.perf_counter()
+            fn()
+            t.append(time.perf_counter() - t0)
+        return min(t)
+
+    t_op = best(lambda: ora.apply_D_sites(Ls, Us, W["csw"], W["kappa"], bs, np.arange(Vs)))
+    t1, t2 = (best(lambda m=m: ora.fgmres(Ls, W["dom"], Us, As, Ais, W["kappa"], bs, 1e-30, m=m, max_restarts=0,
+                                           use_sap=W["sap_prec"] is not None, nmr=W["nmr"], ncy=W["ncy"]))
+              for m in (1, 2))
+    per_it = max(t2 - t1, 0.0)
+    return {"lattice": list(Ls), "per_iteration": per_it / t_op, "fixed": max(t1 - per_it, 0.0) / t_op}
+
+
+def oracle_sample(W, U, b, nsites, seed=11):
+    """One bounded sample of the workload for the FP64 oracle: its operator
+    D = A - kappa H (clover built per site) at nsites sites of the workload's
+    gauge field, applied to the workload's source.  Returns seconds."""
+    from oracle import pyoracle as ora
+
+    V = int(np.prod(W["L"]))
+    sites = np.sort(np.random.Generator(np.random.Philox(seed)).choice(V, size=min(nsites, V), replace=False))
+    x = b if b.ndim == 3 else b[0]
+    t0 = time.perf_counter()
+    ora.apply_D_sites(W["L"], U, W["csw"], W["kappa"], x, sites)
+    return time.perf_counter() - t0
+
+
+def oracle_baseline(W, U, b, nsites, units=None, iters=None, restarts=0):
+    """cpu_baseline record: the measured sample time (ms) as the value, and
+    time-to-solution estimates scaled from it in separately named keys."""
+    V = int(np.prod(W["L"]))
+    nsites = min(nsites, V)
+    t = oracle_sample(W, U, b, nsites)
+    full_op_ms = t / nsites * V * 1e3
+    rec = {"value": t * 1e3, "unit": "ms", "cores": 1, "kind": "oracle",
+           "sample": (f"FP64 oracle operator (clover built per site) at {nsites} sampled sites of the "
+                      f"{'x'.join(map(str, W['L']))} workload's gauge field and source, single thread"),
+           "host": host_info(), "scaled_full_operator_ms": full_op_ms}
+    if units is not None:
+        nr = W.get("nrhs", 1)
+        rec["scaled_ms_per_fgmres_iteration"] = full_op_ms * units["per_iteration"] * nr
+        rec["scaled_ms_fixed"] = full_op_ms * units["fixed"] * nr
+        rec["cost_units_measured_on"] = units["lattice"]
+        if iters is not None:
+            rec["scaled_time_to_solution_ms"] = (rec["scaled_ms_fixed"] * (1 + restarts) +
+                                                 rec["scaled_ms_per_fgmres_iteration"] * iters)
+            rec["scaled_with"] = f"the GPU solve's {iters} iterations and {restarts} restarts"
+    return rec
+
+
+REF_SAMPLE_SITES = 1 << 18
+CPU_SAMPLE_SITES = 1 << 20  # about 15-20 s of single-thread oracle work
 
 
 def run_reference(args):
@@ -240,21 +315,35 @@ def run_reference(args):
         return
     from paper_1502_04025_gb300 import inputs
 
-    U = inputs.gauge_field(WL["L"], WL["eps"], WL["gauge_seed"])
-    vals = []
-    samples = []
+    W = CONFIGS[args.config]
+    U = inputs.gauge_field(W["L"], W["eps"], W["gauge_seed"])
+    b = make_sources(W)
+    units = oracle_cost_units(W)
+    V = int(np.prod(W["L"]))
+    nsites = min(REF_SAMPLE_SITES, V)
+    ms = []
     for k in range(args.warmup + args.steps):
-        s = oracle_sample(WL, U)
+        t = oracle_sample(W, U, b, nsites, seed=11 + k)
         if k >= args.warmup:
-            vals.append(s["value"])
-            samples.append(s)
-    v = statistics.mean(vals)
+            ms.append(t * 1e3)
+    v = statistics.mean(ms)
+    full_op_ms = v / nsites * V
+    cpu = {"value": v, "unit": "ms", "cores": 1, "kind": "oracle",
+           "sample": (f"per step: FP64 oracle operator (clover built per site) at {nsites} sampled sites "
+                      f"of the {'x'.join(map(str, W['L']))} workload's gauge field and source, single thread"),
+           "host": host_info()}
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD_NAME, "lattice": list(WL["L"]), "domain": list(WL["dom"])},
-            "cpu_baseline": {"value": v, "unit": "ms", "cores": 1, "kind": "oracle", "sample": samples[-1]["sample"]},
-            "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "config": {"workload": W["name"], "config": args.config, "lattice": list(W["L"]),
+                       "domain": list(W["dom"])},
+            "cpu_baseline": cpu,
+            "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "sample_sites": nsites,
+            "scaled_full_operator_ms": full_op_ms,
+            "scaled_ms_per_fgmres_iteration": full_op_ms * units["per_iteration"] * W.get("nrhs", 1),
+            "scaled_ms_fixed": full_op_ms * units["fixed"] * W.get("nrhs", 1),
+            "cost_units": units}
     print(json.dumps(line), flush=True)
 
 
@@ -337,6 +426,12 @@ def run_qdd(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
+    # measured FMA-chain peaks (FP64 and FP32), before the timed region
+    fma = {"fp64_tflops": qdd.qdd_measure_fma_peak(local, True, 200.0)[0],
+           "fp32_tflops": qdd.qdd_measure_fma_peak(local, False, 200.0)[0],
+           "how": "qdd_measure_fma_peak: 8 independent FMA chains per thread, 8 CTAs of 256 threads per SM, "
+                  "about 200 ms, CUDA events"}
+
     rep = None
     # per-launch CUDA events on the Schwarz kernel (the dominant class); the
     # event pool is created here, before the timed region
@@ -372,8 +467,25 @@ def run_qdd(args):
     qdd.qdd_get_kernel_times(ctx, reset=True)
     flush.fill_(1.0)
     qdd.qdd_solve(g, bd, params, x=xd, allow_noconv=True)
+    work = qdd.qdd_get_kernel_work(ctx)
     shares = qdd.qdd_get_kernel_times(ctx, reset=True)
     qdd.qdd_set_profiling(ctx, 0)
+
+    # ---- the FP64 vector algebra against its roofline: the time it needs at
+    # the measured FP64 FMA rate or the measured HBM bandwidth, whichever binds
+    blas_ms = shares["blas"][0]
+    blas_flop, blas_bytes = work["blas"]
+    t_alu = blas_flop / (fma["fp64_tflops"] * 1e12) * 1e3
+    t_hbm = blas_bytes / (pk["hbm_gbs"] * 1e9) * 1e3
+    blas_roof = {"kernel": "FP64 vector kernels of one solve (multi-dot, multi-axpy + norm, scaling, solution update)",
+                 "bound": "fp64 alu" if t_alu >= t_hbm else "hbm", "ms": blas_ms, "launches": shares["blas"][1],
+                 "flop": blas_flop, "bytes": blas_bytes,
+                 "achieved_tflops": blas_flop / (blas_ms * 1e-3) / 1e12 if blas_ms > 0 else None,
+                 "achieved_gbs": blas_bytes / (blas_ms * 1e-3) / 1e9 if blas_ms > 0 else None,
+                 "peak_fp64_tflops": fma["fp64_tflops"], "peak_hbm_gbs": pk["hbm_gbs"],
+                 "frac": max(t_alu, t_hbm) / blas_ms if blas_ms > 0 else None,
+                 "frac_is": "roofline time (max of flop / measured FP64 FMA rate, bytes / measured HBM) over the "
+                            "event-timed time"}
 
     # ---- roofline of the dominant kernel class (timed inside the timed region)
     classes = {k: v for k, v in shares.items() if v[1] > 0}
@@ -390,7 +502,7 @@ def run_qdd(args):
                 if W["sap_prec"] != "f64" else "k_sap (Schwarz colour half-sweep, FP64)",
                 "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak,
-                "traffic": ncu_traffic("k_sap") if args.config == 2 else None,
+                "traffic": ncu_traffic(f"k_sap_config{args.config}"),
                 "ms_per_launch": ms_launch, "launches": kt["sap"][1],
                 "flop_per_launch": flop,
                 "peak_source": f"{sm_count} SMs x 128 FP32 lanes x 2 flop x {pk.get('sm_max_mhz', 2070.0):.0f} MHz"}
@@ -426,7 +538,7 @@ def run_qdd(args):
     e2e = {"value": statistics.mean(e2e_ms) if e2e_ms else None, "unit": "ms",
            "h2d_bytes_per_step": int(bh.nbytes), "d2h_bytes_per_step": int(xh.nbytes), "host_memory": "pinned"}
     parity = None
-    if rank == 0 and args.config != 2 and e2e_ms:
+    if rank == 0 and e2e_ms:
         parity = sampled_residual(W, U, b, xh)
 
     # ---- batching: the same sources one at a time (the first source's solve, times nrhs)
@@ -454,7 +566,7 @@ def run_qdd(args):
     # Arnoldi operator): the plain FP64 GPU path the mixed-precision one is
     # measured against
     plain = None
-    if rank == 0 and args.config == 2 and not args.no_fp64_compare:
+    if rank == 0 and args.config in (2, 4) and not args.no_fp64_compare:
         p64 = qdd.qdd_default_params(tol=W["tol"], restart_m=W["m"], nmr=W["nmr"], ncy=W["ncy"], sap_prec="f64",
                                      arnoldi_prec="f64", max_restarts=200, nrhs=nrhs, reorth=1)
         qdd.qdd_solve(g, bd, p64, x=xd, allow_noconv=True)
@@ -472,8 +584,7 @@ def run_qdd(args):
 
     # ---- full-lattice operator throughput (FP32 and FP16 storage) on a lattice > L2
     dslash = None
-    if not args.no_dslash and rank == 0 and args.config == 2:
-        del U
+    if not args.no_dslash and rank == 0 and args.config in (2, 4):
         Ud = inputs.gauge_field(DSL["L"], DSL["eps"], DSL["gauge_seed"])
         gd = qdd.qdd_create_gauge_field(ctx, DSL["L"], DSL["dom"], Ud)
         del Ud
@@ -484,7 +595,7 @@ def run_qdd(args):
         two_rows, _ = qdd.qdd_link_compression(gd)
         dslash = {"lattice": list(DSL["L"]), "flop_per_site": 1848,
                   "link_rows": 2 if two_rows else 3}
-        for name in ("f32", "f32_three_rows", "h16", "f16", "df64", "f64"):
+        for name in ("f32", "f32_three_rows", "h16", "f16", "bf16", "df64", "f64"):
             prec = name.split("_")[0]
             rows3 = name.endswith("three_rows") or not two_rows
             qdd.qdd_set_link_compression(gd, not rows3)
@@ -504,12 +615,14 @@ def run_qdd(args):
                             "bytes_per_site": bps}
         qdd.qdd_set_link_compression(gd, two_rows)
         qdd.qdd_destroy_gauge(gd)
-        U = None
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.config == 2:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            cpu = oracle_sample(WL, U)
+            if U is None:
+                U = inputs.gauge_field(W["L"], W["eps"], W["gauge_seed"])
+            cpu = oracle_baseline(W, U, b, CPU_SAMPLE_SITES, oracle_cost_units(W), reps[-1]["iters"],
+                                  reps[-1]["restarts"])
         except Exception as e:  # the GPU number stands without it
             cpu = {"value": None, "unit": "ms", "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
 
@@ -530,7 +643,8 @@ def run_qdd(args):
                            "parallelism": f"{world} replica(s)"},
                 "iters": last["iters"], "restarts": last["restarts"], "true_rel_res": last["true_rel_res"],
                 "converged": bool(last["converged"]),
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+                "roofline": roof, "roofline_fp64_vector_algebra": blas_roof, "fma_peaks": fma,
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
                 "dslash": dslash, "plain_fp64": plain, "unbatched": unbatched}
         if parity is not None:
             line["parity"] = parity

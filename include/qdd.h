@@ -151,6 +151,24 @@ qdd_status qdd_set_profiling(qdd_ctx *ctx, int classes);
  * operator kernels, out[4..5] of FP64 vector kernels.  reset != 0 zeroes them. */
 qdd_status qdd_get_kernel_times(qdd_ctx *ctx, double out[6], int reset);
 
+/*
+ * Measured arithmetic peak of device `device` (not part of the method: the
+ * denominator of the rooflines of the ALU-bound steps).  Runs a chain of
+ * independent fused multiply-adds on every SM, in FP64 (fp64 != 0) or FP32,
+ * for about target_ms milliseconds (0 < target_ms <= 10000), timed with CUDA
+ * events; *tflops = 2 flop per FMA / elapsed time, *ms (may be NULL) = the
+ * elapsed time.  Synchronous; allocates and frees a small output buffer.
+ */
+qdd_status qdd_measure_fma_peak(int device, int fp64, double target_ms, double *tflops, double *ms);
+
+/* Algorithmic work of the kernels launched since the last reset of
+ * qdd_get_kernel_times: out[0..1] = (flop, bytes) of SAP block kernels,
+ * out[2..3] of full-lattice operator kernels, out[4..5] of FP64 vector
+ * kernels.  Only the FP64 vector kernels count theirs (8 flop per complex
+ * multiply-add; 16 bytes per FP64 and 8 per FP32 complex element read or
+ * written once); the other classes report 0. */
+qdd_status qdd_get_kernel_work(qdd_ctx *ctx, double out[6]);
+
 /* Bytes of device memory the context holds now, and its budget. */
 qdd_status qdd_memory(qdd_ctx *ctx, size_t *used, size_t *budget);
 
@@ -338,7 +356,10 @@ qdd_status qdd_cdot_multi(qdd_ctx *ctx, const double *v, int nvec, int64_t ld, c
  * All calls share the array: calls that overlap on the GPU (other streams,
  * other host threads) race and must be serialised by the caller.  Nothing in
  * the array needs to start at zero; each call overwrites what it reads.
- * Arguments and layout as for qdd_cdot_multi; returns after out is written.
+ * Arguments and layout as for qdd_cdot_multi.  Unlike the other entry points
+ * this one does not wait for its result: it returns once its kernels are
+ * queued on `stream`, and out is ready in that stream's order (synchronise the
+ * stream, or order later work after it, before reading out).
  */
 qdd_status qdd_cdot_multi_noalloc(const double *v, int nvec, int64_t ld, const double *w, int64_t n,
                                   double *out, void *stream);

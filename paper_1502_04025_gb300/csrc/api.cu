@@ -63,6 +63,13 @@ void Timer::count(int cls)
     launches[cls]++;
 }
 
+void Timer::work(int cls, double f, double b)
+{
+    std::lock_guard<std::mutex> lk(mu);
+    flop[cls] += f;
+    bytes[cls] += b;
+}
+
 void Timer::end(int cls, cudaStream_t s, cudaEvent_t a)
 {
     if (!a) return;
@@ -313,7 +320,20 @@ qdd_status qdd_get_kernel_times(qdd_ctx *ctx, double out[6], int reset)
             ctx->timer.ms[c] = 0;
             ctx->timer.launches[c] = 0;
             ctx->timer.timed[c] = 0;
+            ctx->timer.flop[c] = 0;
+            ctx->timer.bytes[c] = 0;
         }
+    return QDD_OK;
+}
+
+qdd_status qdd_get_kernel_work(qdd_ctx *ctx, double out[6])
+{
+    if (!ctx || !out) return QDD_EINVAL;
+    std::lock_guard<std::mutex> lk(ctx->timer.mu);
+    for (int c = 0; c < 3; c++) {
+        out[2 * c] = ctx->timer.flop[c];
+        out[2 * c + 1] = ctx->timer.bytes[c];
+    }
     return QDD_OK;
 }
 

@@ -293,6 +293,7 @@ qdd_status blas_cdot_multi(Ctx *ctx, const double2 *v, int nvec, int64_t ld, con
     const int nb = blas_blocks(ctx, n);
     for (int j0 = 0; j0 < nvec; j0 += kNV) {
         int nv = nvec - j0 < kNV ? nvec - j0 : kNV;
+        ctx->timer.work(K_BLAS, 8.0 * nv * n, 16.0 * (nv + 1) * n);
         LaunchScope ls(ctx->timer, K_BLAS, s);
         nv_dispatch(nv, [&](auto c) {
             k_cdot_partial<decltype(c)::value><<<nb, kBT, 0, s>>>(v + j0 * ld, nv, ld, w, n, scratch,
@@ -311,6 +312,9 @@ qdd_status blas_caxpy_multi_norm(Ctx *ctx, const double2 *v, int nvec, int64_t l
     do {
         int nv = nvec - j0 < kNV ? nvec - j0 : kNV;
         bool last = j0 + nv >= nvec;
+        // v read, w read and (when updated) written; |w|^2 on the last pass
+        ctx->timer.work(K_BLAS, 8.0 * nv * n + ((last && norm2_out) ? 4.0 * n : 0.0),
+                        16.0 * (nv + 1 + (nv > 0 ? 1 : 0)) * n);
         {
             LaunchScope ls(ctx->timer, K_BLAS, s);
             double2 *part = (last && norm2_out) ? scratch : nullptr;
@@ -340,6 +344,7 @@ qdd_status blas_scale_by_norm(Ctx *ctx, const double2 *w, int64_t n, const doubl
     // one element per thread: a memory-bound pass needs every load in flight
     // at once (the reduction kernels' two blocks per SM keep too few)
     const int64_t nb = (n + kBT - 1) / kBT;
+    ctx->timer.work(K_BLAS, 2.0 * n, (32.0 + (out32 ? 8.0 : 0.0)) * n);
     LaunchScope ls(ctx->timer, K_BLAS, s);
     k_scale_by_norm<<<(unsigned)(nb < (1LL << 30) ? nb : (1LL << 30)), kBT, 0, s>>>(w, n, norm2, out, out32);
     QDD_CUDA(cudaGetLastError());
@@ -353,6 +358,8 @@ qdd_status blas_combine(Ctx *ctx, const void *src, bool src_f32, int nsrc, int64
     const int nb = blas_blocks(ctx, n);
     for (int c0 = 0; c0 < ncols; c0 += kNV) {
         int nc = ncols - c0 < kNV ? ncols - c0 : kNV;
+        ctx->timer.work(K_BLAS, 8.0 * nsrc * nc * n,
+                        ((src_f32 ? 8.0 : 16.0) * nsrc + 16.0 * nc * (accumulate ? 2 : 1)) * n);
         LaunchScope ls(ctx->timer, K_BLAS, s);
         nv_dispatch(nc, [&](auto c) {
             if (src_f32)
@@ -372,6 +379,7 @@ qdd_status blas_axpy_multi(Ctx *ctx, const void *z, bool z_f32, int nvec, int64_
                            double2 *x, int64_t n, cudaStream_t s)
 {
     if (nvec <= 0) return QDD_OK;
+    ctx->timer.work(K_BLAS, 8.0 * nvec * n, ((z_f32 ? 8.0 : 16.0) * nvec + 32.0) * n);
     LaunchScope ls(ctx->timer, K_BLAS, s);
     if (z_f32)
         k_axpy_multi<float2><<<blas_blocks(ctx, n), kBT, 0, s>>>((const float2 *)z, nvec, ld, coef, x, n);
@@ -474,7 +482,7 @@ extern "C" qdd_status qdd_cdot_multi_noalloc(const double *v, int nvec, int64_t 
         });
         k_reduce_final<<<nv, kBT, 0, s>>>(part, nb, kNV, O2 + j0, 0);
     }
+    // no synchronisation: out is ready in the order of `stream`
     QDD_CUDA(cudaGetLastError());
-    QDD_CUDA(cudaStreamSynchronize(s));
     return QDD_OK;
 }

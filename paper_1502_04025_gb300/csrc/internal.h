@@ -51,6 +51,9 @@ struct Timer {
     long long launches[4] = {0, 0, 0, 0};
     double ms[4] = {0, 0, 0, 0};
     long long timed[4] = {0, 0, 0, 0};
+    // algorithmic work of the launches (counted where a launcher states it)
+    double flop[4] = {0, 0, 0, 0};
+    double bytes[4] = {0, 0, 0, 0};
     struct Pending {
         cudaEvent_t a, b;
         int cls;
@@ -63,6 +66,7 @@ struct Timer {
     void begin(int cls, cudaStream_t s, cudaEvent_t *a);
     void begin_seq(int cls, cudaStream_t s, cudaEvent_t *a);  // events, no launch count
     void count(int cls);                                      // launch count only
+    void work(int cls, double f, double b);                   // add algorithmic flop and bytes
     void end(int cls, cudaStream_t s, cudaEvent_t a);
     void resolve();  // after the stream has been synchronised
     ~Timer();

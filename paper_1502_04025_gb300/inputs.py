@@ -12,12 +12,19 @@ Host layouts (the library's public layout):
 * spinors     psi[n, s, c], spin s = 0..3, colour c = 0..2
 
 Gauge recipe: U = exp(i*eps*H) with H = sum_a h_a lambda_a / 2, h_a ~ N(0,1)
-(lambda_a the Gell-Mann matrices), computed from the eigen-decomposition of
-the Hermitian H, then re-unitarised by Gram-Schmidt and phase-fixed to
-det U = 1.  Random numbers come from numpy's Philox counter-based generator
-keyed by the seed, drawn in site-major order (n, mu, a).
+(lambda_a the Gell-Mann matrices), then re-unitarised by Gram-Schmidt and
+phase-fixed to det U = 1.  Random numbers come from numpy's Philox
+counter-based generator keyed by the seed, drawn in site-major order
+(n, mu, a).  The matrix exponential and the re-unitarisation run in the
+small C helper su3gen.c (Taylor series with scaling and squaring, OpenMP
+over links), built with gcc on first use: a 48^3x96 field has 42 million
+links, which numpy's per-matrix eigen-decomposition takes minutes for.
 """
 from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
 
 import numpy as np
 
@@ -79,8 +86,45 @@ def _reunitarise(u: np.ndarray) -> np.ndarray:
     return out * phase[..., None, None]
 
 
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_GEN_SRC = os.path.join(_HERE, "su3gen.c")
+_GEN_LIB = os.path.join(_HERE, "libsu3gen.so")
+_gen = None
+
+
+def build_generator(force: bool = False) -> str:
+    """Compile su3gen.c into libsu3gen.so (gcc, OpenMP, no contracted FMAs)."""
+    if not force and os.path.exists(_GEN_LIB) and os.path.getmtime(_GEN_LIB) >= os.path.getmtime(_GEN_SRC):
+        return _GEN_LIB
+    tmp = _GEN_LIB + f".tmp{os.getpid()}"
+    subprocess.run(["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", "-o", tmp,
+                    _GEN_SRC, "-lm"], check=True)
+    os.replace(tmp, _GEN_LIB)
+    return _GEN_LIB
+
+
+def _generator():
+    global _gen
+    if _gen is None:
+        build_generator()
+        lib = ctypes.CDLL(_GEN_LIB)
+        lib.su3gen_from_normals.argtypes = [ctypes.c_long, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p]
+        lib.su3gen_from_normals.restype = ctypes.c_int
+        _gen = lib
+    return _gen
+
+
 def _su3_from_normals(h: np.ndarray, eps: float) -> np.ndarray:
-    """exp(i*eps*sum_a h_a lambda_a/2) for h of shape (..., 8)."""
+    """exp(i*eps*sum_a h_a lambda_a/2), re-unitarised, for h of shape (..., 8)."""
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    out = np.empty(h.shape[:-1] + (3, 3), dtype=np.complex128)
+    assert _generator().su3gen_from_normals(h.size // 8, h.ctypes.data, float(eps), out.ctypes.data) == 0
+    return out
+
+
+def su3_from_normals_eigh(h: np.ndarray, eps: float) -> np.ndarray:
+    """The same matrices through numpy's eigen-decomposition of H (slow; a
+    cross-check of the C helper in the tests)."""
     lam = gell_mann()
     H = np.einsum("...a,aij->...ij", h, lam) * 0.5
     w, W = np.linalg.eigh(H)

@@ -74,7 +74,9 @@ _SIGS = {
     "qdd_last_error": (ctypes.c_char_p, []),
     "qdd_set_profiling": (ctypes.c_int, [_vp, ctypes.c_int]),
     "qdd_get_kernel_times": (ctypes.c_int, [_vp, _dp, ctypes.c_int]),
+    "qdd_get_kernel_work": (ctypes.c_int, [_vp, _dp]),
     "qdd_memory": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
+    "qdd_measure_fma_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp, _dp]),
     "qdd_create_gauge_field": (ctypes.c_int, [_vp, _ip, _ip, _vp, ctypes.c_int, ctypes.POINTER(_vp)]),
     "qdd_destroy_gauge": (None, [_vp]),
     "qdd_set_link_compression": (ctypes.c_int, [_vp, ctypes.c_int]),
@@ -199,10 +201,26 @@ def qdd_get_kernel_times(ctx, reset: bool = False) -> dict:
     return {"sap": (out[0], int(out[1])), "dslash": (out[2], int(out[3])), "blas": (out[4], int(out[5]))}
 
 
+def qdd_get_kernel_work(ctx) -> dict:
+    """Algorithmic (flop, bytes) per kernel class since the last reset of
+    qdd_get_kernel_times (only the FP64 vector kernels count theirs)."""
+    out = (ctypes.c_double * 6)()
+    _check(_lib.qdd_get_kernel_work(ctx, out), "qdd_get_kernel_work")
+    return {"sap": (out[0], out[1]), "dslash": (out[2], out[3]), "blas": (out[4], out[5])}
+
+
 def qdd_memory(ctx):
     u, b = ctypes.c_size_t(), ctypes.c_size_t()
     _check(_lib.qdd_memory(ctx, ctypes.byref(u), ctypes.byref(b)), "qdd_memory")
     return u.value, b.value
+
+
+def qdd_measure_fma_peak(device: int = 0, fp64: bool = True, target_ms: float = 200.0):
+    """(TFLOP/s, ms) of the FMA-chain kernel in FP64 or FP32 on `device`."""
+    t, ms = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.qdd_measure_fma_peak(device, 1 if fp64 else 0, float(target_ms), ctypes.byref(t), ctypes.byref(ms)),
+           "qdd_measure_fma_peak")
+    return t.value, ms.value
 
 
 # ------------------------------------------------------------ gauge field
@@ -296,6 +314,7 @@ def qdd_cdot_multi(ctx, v, w):
     import torch
 
     assert v.is_cuda and w.is_cuda and v.dtype == torch.complex128 and w.dtype == torch.complex128
+    assert v.dim() == 2 and v.stride(1) == 1 and w.is_contiguous(), "rows of v and w must be contiguous"
     nvec, n = v.shape
     out = torch.empty(nvec, dtype=torch.complex128, device=v.device)
     _check(_lib.qdd_cdot_multi(ctx, v.data_ptr(), nvec, v.stride(0), w.data_ptr(), n, out.data_ptr(),
@@ -305,10 +324,13 @@ def qdd_cdot_multi(ctx, v, w):
 
 def qdd_cdot_multi_noalloc(v, w, out=None):
     """<v_i, w> without any device allocation inside the library (torch CUDA
-    complex128 tensors; out, if given, is a CUDA tensor of nvec elements)."""
+    complex128 tensors; out, if given, is a CUDA tensor of nvec elements).
+    The call does not wait: out is ready in the order of torch's current
+    stream, which every later torch operation on that stream respects."""
     import torch
 
     assert v.is_cuda and w.is_cuda and v.dtype == torch.complex128 and w.dtype == torch.complex128
+    assert v.dim() == 2 and v.stride(1) == 1 and w.is_contiguous(), "rows of v and w must be contiguous"
     nvec, n = v.shape
     if out is None:
         out = torch.empty(nvec, dtype=torch.complex128, device=v.device)

@@ -42,15 +42,21 @@ def test_operator_flop_decomposition():
 
 
 def test_sap_flop_per_site():
-    # per even/odd pair: setup (clover + hops + combine on the odd site's reconstruction input), nmr MR
-    # steps of two full applies plus the MR vector algebra, and the final reconstruction; then
-    # the entering hops of the inflow
-    full = 1320 + 504 + 24
-    pair = full + 4 * (2 * full + 336) + full
-    assert bench.sap_flop_per_site((8, 4, 4, 4), 4) == pytest.approx(pair / 2 + 1.75 * 168)
-    assert bench.sap_flop_per_site((8, 4, 4, 4), 4) == pytest.approx(10206.0)
+    # inside a domain only the hops that stay in it are computed (Dirichlet boundary): an 8x4^3 domain
+    # loses 1.75 of its 8 hops per site, a 4^4 domain 2; each hop is 144 flop and their sum takes one
+    # spinor add (24) fewer than there are hops
+    assert 8 * 144 + 7 * 24 == bench.SAP_FLOP["hop"]
+    for dom, c in (((8, 4, 4, 4), 1.75), ((4, 4, 4, 4), 2.0)):
+        hops = (8 - c) * 144 + (7 - c) * 24
+        full = hops + 504 + 24
+        # per even/odd pair: setup (odd clover; even hops + combine), nmr MR steps of two in-domain applies
+        # plus the MR vector algebra, the reconstruction; then the inflow's entering hops
+        pair = (504 + hops + 24) + 4 * (2 * full + 336) + full
+        assert bench.sap_flop_per_site(dom, 4) == pytest.approx(pair / 2 + c * 168)
+    assert bench.sap_flop_per_site((8, 4, 4, 4), 4) == pytest.approx(8736.0)
+    assert bench.sap_flop_per_site((4, 4, 4, 4), 4) == pytest.approx(8568.0)
     # one launch sweeps half the sites: the 16^3x32 workload's flop per launch
-    assert 16 * 16 * 16 * 32 // 2 * bench.sap_flop_per_site((8, 4, 4, 4), 4) == pytest.approx(668860416.0)
+    assert 16 * 16 * 16 * 32 // 2 * bench.sap_flop_per_site((8, 4, 4, 4), 4) == pytest.approx(572522496.0)
 
 
 def test_operator_bytes_per_site():
@@ -61,8 +67,8 @@ def test_operator_bytes_per_site():
 
 
 def test_traffic_record_only_while_sources_match(tmp_path, monkeypatch):
-    rec = json.load(open(os.path.join(bench.ROOT, "profiles", "traffic.json")))["k_sap"]
-    assert bench.ncu_traffic("k_sap") == rec["dram_bytes_per_launch"]
+    rec = json.load(open(os.path.join(bench.ROOT, "profiles", "traffic.json")))["k_sap_config2"]
+    assert bench.ncu_traffic("k_sap_config2") == rec["dram_bytes_per_launch"]
     # a copy of the tree whose kernel source differs by one byte
     (tmp_path / "profiles").mkdir()
     shutil.copy(os.path.join(bench.ROOT, "profiles", "traffic.json"), tmp_path / "profiles" / "traffic.json")
@@ -71,8 +77,8 @@ def test_traffic_record_only_while_sources_match(tmp_path, monkeypatch):
         dst.parent.mkdir(parents=True, exist_ok=True)
         shutil.copy(os.path.join(bench.ROOT, src), dst)
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench.ncu_traffic("k_sap") == rec["dram_bytes_per_launch"]
+    assert bench.ncu_traffic("k_sap_config2") == rec["dram_bytes_per_launch"]
     with open(tmp_path / rec["sources"][0], "a") as f:
         f.write("\n")
-    assert bench.ncu_traffic("k_sap") is None
+    assert bench.ncu_traffic("k_sap_config2") is None
     assert bench.ncu_traffic("no_such_kernel") is None

@@ -24,7 +24,7 @@ def test_gauge_field_is_su3():
 
 def test_zero_eps_gives_unit_links():
     U = inputs.gauge_field((4, 4, 4, 4), 0.0, 1002).reshape(-1, 3, 3)
-    assert np.abs(U - np.eye(3)).max() <= 1e-14  # W W^+ from the eigendecomposition, to rounding
+    assert np.abs(U - np.eye(3)).max() <= 1e-14
 
 
 def test_third_row_is_the_conjugated_cross_product():
@@ -45,3 +45,14 @@ def test_sources():
     assert np.array_equal(np.nonzero(P)[1], 5 * 12 + np.arange(12))  # site 5, spin*3 + colour in order
     g = inputs.gaussian_source(L, 2001)
     assert abs(g.real.std() - 1) < 0.05 and abs(g.imag.std() - 1) < 0.05
+
+
+def test_exponential_matches_the_eigendecomposition():
+    """The C helper's Taylor series with scaling and squaring gives the same
+    SU(3) matrices as exp(i eps H) through numpy's eigen-decomposition of H,
+    for small and large eps (several squarings)."""
+    h = inputs.rng(77).standard_normal((4000, 4, 8))
+    for eps in (0.1, 0.7, 3.0):
+        a = inputs._su3_from_normals(h, eps)
+        b = inputs.su3_from_normals_eigh(h, eps)
+        assert np.abs(a - b).max() <= 1e-14
