@@ -216,6 +216,17 @@ qdd_status qdd_link_compression(qdd_gauge *g, int *two_rows, int *is_su3);
 qdd_status qdd_check_hits(unsigned long long *hits);
 
 /*
+ * Range-checked build only (test aid for the device-side failure path): the
+ * poll limit of the Schwarz kernel's first bounded wait, the one for the
+ * staging of a domain's links and clover, on device `device` (default
+ * 1 << 22).  With 0 the wait gives up at once: the kernel sets its timeout
+ * flag, waits (with its own fixed limit) until its staging copies have
+ * landed, and returns, and the calling entry point reports QDD_ETIMEOUT.
+ * Nothing spins without a limit.  The normal build returns QDD_EINVAL.
+ */
+qdd_status qdd_check_set_wait_limit(int device, unsigned spins);
+
+/*
  * Build the clover term A = 1 + i kappa c_sw sum sigma F (two Hermitian 6x6
  * chirality blocks per site) and the inverse blocks on odd sites used by the
  * even-odd domain solver (Sec. 3.1, footnote on the domain inversion).  Must

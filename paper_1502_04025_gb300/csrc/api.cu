@@ -458,6 +458,20 @@ qdd_status qdd_check_hits(unsigned long long *hits)
 #endif
 }
 
+qdd_status qdd_check_set_wait_limit(int device, unsigned spins)
+{
+    clear_error();
+#ifdef QDD_CHECK
+    QDD_CUDA(cudaSetDevice(device));
+    return set_first_wait_spins_sap(spins);
+#else
+    (void)device;
+    (void)spins;
+    set_error("this library was built without range checks (QDD_CHECK)");
+    return QDD_EINVAL;
+#endif
+}
+
 qdd_status qdd_link_compression(qdd_gauge *g, int *two_rows, int *is_su3)
 {
     clear_error();

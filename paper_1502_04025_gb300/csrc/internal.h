@@ -280,6 +280,7 @@ struct SapBuffers {
 size_t sap_face_bytes(const HostGeom &hg, qdd_prec prec, int nrhs);
 // out-of-range indices skipped by the range-checked build's kernels (0 otherwise)
 unsigned long long check_hits_sap();
+qdd_status set_first_wait_spins_sap(unsigned spins);
 unsigned long long check_hits_dslash();
 unsigned long long check_hits_mg();
 qdd_status launch_sap_halfsweep(Gauge *g, qdd_prec prec, const SapBuffers &b, int colour, int nmr, int nrhs,

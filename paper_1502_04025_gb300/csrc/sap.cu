@@ -114,6 +114,17 @@ __device__ __forceinline__ void bulk_g2s_chunked(void *dst, const void *src, uin
     }
 }
 
+// Poll limit of the first bounded wait of a visit (the staging of links and
+// clover).  The range-checked build lets a test lower it, so that the wait
+// gives up and the timeout path runs: the kernel flags the error, lets its
+// copies land within the drain wait's own limit and leaves.
+#ifdef QDD_CHECK
+static __device__ unsigned g_first_wait_spins = 1u << 22;
+#define QDD_FIRST_WAIT_SPINS g_first_wait_spins
+#else
+#define QDD_FIRST_WAIT_SPINS (1u << 22)
+#endif
+
 // ---------------------------------------------------------- kernel state
 
 template <typename R, typename SL, typename SC, typename SS, typename SP>
@@ -462,7 +473,7 @@ __global__ void __launch_bounds__(256) k_sap(const SapArgs<R, SL, SC, SS, SP> a)
         const int64_t rb = rr * a.rstride, sb = rr * a.sstride;
 
         if ((STL || STC) && rr == 0) {
-            bool ok = mbar_wait_bounded(bar, 0, 1u << 22);
+            bool ok = mbar_wait_bounded(bar, 0, QDD_FIRST_WAIT_SPINS);
             if (!ok) atomicOr(a.err, kErrMbarTimeout);
             if (__syncthreads_or(!ok)) {
                 // give the copies in flight a last bounded chance to land, then leave
@@ -793,6 +804,20 @@ static qdd_status dispatch_staging(Gauge *g, const SapArgs<R, SL, SC, SS, SP> &a
         return run_sap<R, SL, SC, SS, SP, false, false>(g, a, s, pdl, timed);
     set_error("domain of %d sites does not fit in shared memory", Vd);
     return QDD_EINVAL;
+}
+
+// the first wait's poll limit on the current device (QDD_CHECK builds)
+qdd_status set_first_wait_spins_sap(unsigned spins)
+{
+#ifdef QDD_CHECK
+    QDD_CUDA(cudaMemcpyToSymbol(g_first_wait_spins, &spins, sizeof(spins)));
+    QDD_CUDA(cudaDeviceSynchronize());
+    return QDD_OK;
+#else
+    (void)spins;
+    set_error("this library was built without range checks (QDD_CHECK)");
+    return QDD_EINVAL;
+#endif
 }
 
 // out-of-range indices the kernels of this file have skipped (QDD_CHECK builds)

@@ -82,6 +82,7 @@ _SIGS = {
     "qdd_set_link_compression": (ctypes.c_int, [_vp, ctypes.c_int]),
     "qdd_link_compression": (ctypes.c_int, [_vp, _ip, _ip]),
     "qdd_check_hits": (ctypes.c_int, [ctypes.POINTER(ctypes.c_ulonglong)]),
+    "qdd_check_set_wait_limit": (ctypes.c_int, [ctypes.c_int, ctypes.c_uint]),
     "qdd_set_clover": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double]),
     "qdd_get_clover": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
     "qdd_apply_D": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp]),
@@ -254,6 +255,12 @@ def qdd_check_hits() -> int:
     h = ctypes.c_ulonglong()
     _check(_lib.qdd_check_hits(ctypes.byref(h)), "qdd_check_hits")
     return h.value
+
+
+def qdd_check_set_wait_limit(device: int, spins: int):
+    """Range-checked build only: poll limit of the Schwarz kernel's first
+    bounded wait (raises QddError with the normal build)."""
+    _check(_lib.qdd_check_set_wait_limit(device, int(spins)), "qdd_check_set_wait_limit")
 
 
 def qdd_set_clover(g, c_sw: float, kappa: float):

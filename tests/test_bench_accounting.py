@@ -5,7 +5,6 @@ traffic record, which is reported only while the kernel's sources match."""
 import itertools
 import json
 import os
-import shutil
 
 import pytest
 
@@ -67,18 +66,20 @@ def test_operator_bytes_per_site():
 
 
 def test_traffic_record_only_while_sources_match(tmp_path, monkeypatch):
-    rec = json.load(open(os.path.join(bench.ROOT, "profiles", "traffic.json")))["k_sap_config2"]
-    assert bench.ncu_traffic("k_sap_config2") == rec["dram_bytes_per_launch"]
-    # a copy of the tree whose kernel source differs by one byte
+    """A DRAM-traffic record names the sources of its kernel with their
+    SHA-256; the bench reports it only while those files are unchanged."""
+    import hashlib
+
+    src = tmp_path / "csrc" / "kernel.cu"
+    src.parent.mkdir(parents=True)
+    src.write_text("__global__ void k() {}\n")
     (tmp_path / "profiles").mkdir()
-    shutil.copy(os.path.join(bench.ROOT, "profiles", "traffic.json"), tmp_path / "profiles" / "traffic.json")
-    for src in rec["sources"]:
-        dst = tmp_path / src
-        dst.parent.mkdir(parents=True, exist_ok=True)
-        shutil.copy(os.path.join(bench.ROOT, src), dst)
+    rec = {"k_example": {"sources": ["csrc/kernel.cu"], "sha256": hashlib.sha256(src.read_bytes()).hexdigest(),
+                         "dram_bytes_per_launch": 12345}}
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(rec))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench.ncu_traffic("k_sap_config2") == rec["dram_bytes_per_launch"]
-    with open(tmp_path / rec["sources"][0], "a") as f:
+    assert bench.ncu_traffic("k_example") == 12345
+    with open(src, "a") as f:
         f.write("\n")
-    assert bench.ncu_traffic("k_sap_config2") is None
+    assert bench.ncu_traffic("k_example") is None
     assert bench.ncu_traffic("no_such_kernel") is None

@@ -3,8 +3,10 @@ on every test geometry and reports no out-of-range index: the Schwarz
 kernel's stencil, face-slot and reduction accesses in every storage
 precision (whole and partial warps, staged and unstaged fields), the
 full-lattice operators with whole and two-row links, a mixed-precision
-solve and a multigrid setup.  The checked build runs in a child process,
-since one process loads one build of the library."""
+solve and a multigrid setup.  It also makes the Schwarz kernel's first
+bounded wait give up (its poll limit set to 0), which must come back as
+QDD_ETIMEOUT and leave the gauge object usable.  The checked build runs in a
+child process, since one process loads one build of the library."""
 import os
 import subprocess
 import sys
@@ -57,3 +59,45 @@ def test_range_checked_build_sees_no_out_of_range_index():
     assert r.returncode == 0, r.stdout + r.stderr
     hits = [line for line in r.stdout.splitlines() if line.startswith("HITS")]
     assert hits == ["HITS 0"], r.stdout + r.stderr
+
+
+CHILD_TIMEOUT = r'''
+import numpy as np
+from paper_1502_04025_gb300 import inputs, qdd
+assert qdd.LIB_PATH.endswith("libqdd_check.so")
+ctx = qdd.qdd_create(0, 0)
+L, dom = (8, 8, 8, 8), (4, 4, 4, 4)
+g = qdd.qdd_create_gauge_field(ctx, L, dom, inputs.gauge_field(L, 0.5, 1001))
+qdd.qdd_set_clover(g, 1.0, 0.12)
+eta = inputs.gaussian_source(L, 2001)
+ref = qdd.qdd_sap_apply(g, eta, 4, 4, "f32")
+qdd.qdd_check_set_wait_limit(0, 0)
+try:
+    qdd.qdd_sap_apply(g, eta, 4, 4, "f32")
+    print("STATUS", qdd.QDD_OK)
+except qdd.QddError as e:
+    print("STATUS", e.status)
+qdd.qdd_check_set_wait_limit(0, 1 << 22)
+again = qdd.qdd_sap_apply(g, eta, 4, 4, "f32")
+print("SAME", bool(np.array_equal(again, ref)))
+x, rep = qdd.qdd_solve(g, eta, tol=1e-10, sap_prec="f32")
+print("CONVERGED", bool(rep["converged"]))
+'''
+
+
+def test_device_wait_that_runs_out_is_reported_and_the_gauge_stays_usable():
+    """The first bounded wait of every Schwarz CTA gives up at once (poll
+    limit 0): each CTA flags the timeout, waits with the drain wait's own
+    limit until its staging copies have landed, and leaves.  qdd_sap_apply
+    reports QDD_ETIMEOUT; with the default limit back, the same call gives
+    the same bits as before and a solve on the same gauge object converges."""
+    from paper_1502_04025_gb300 import build
+
+    build.build(check=True)
+    env = dict(os.environ, QDD_CHECKED="1")
+    r = subprocess.run([sys.executable, "-c", CHILD_TIMEOUT], cwd=ROOT, env=env, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
+    out = dict(line.split(" ", 1) for line in r.stdout.splitlines() if " " in line)
+    assert out.get("STATUS") == "6", r.stdout + r.stderr  # QDD_ETIMEOUT
+    assert out.get("SAME") == "True" and out.get("CONVERGED") == "True", r.stdout + r.stderr

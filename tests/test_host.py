@@ -132,6 +132,10 @@ def test_no_gpu_needed_for_errors(qdd):
     # the normal build has no range checks to report
     with pytest.raises(qdd.QddError):
         qdd.qdd_check_hits()
+    # nor a wait limit to lower
+    with pytest.raises(qdd.QddError) as e:
+        qdd.qdd_check_set_wait_limit(0, 0)
+    assert e.value.status == qdd.QDD_EINVAL
 
 
 def _coords(L, n):
