@@ -18,9 +18,12 @@ same gauge field and source, one sample per step; the line's value is that
 measured time.  Time-to-solution estimates scaled from the sample are in
 separately named keys.
 
-Under torchrun (--gpus N) every rank solves its own copy of the workload
-(replicas), the timed region is bracketed by barriers, and the slowest
-rank's time is reported.
+Under torchrun (--gpus N) the lattice is sharded in t over the ranks (slabs
+of whole domains; face slots and boundary planes exchanged, dot products
+summed over the ranks: strong scaling) when it splits into equal slabs of an
+even number of domain blocks, else (or with --replicas) every rank solves its
+own copy of the workload (weak scaling).  The timed region is bracketed by
+barriers, and the slowest rank's time is reported.
 """
 from __future__ import annotations
 
@@ -96,6 +99,8 @@ def parse():
     ap.add_argument("--no-dslash", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true", help="skip the plain FP64 path on the same system")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--replicas", action="store_true",
+                    help="with several GPUs, solve one copy of the workload per GPU instead of sharding it")
     return ap.parse_args()
 
 
@@ -416,7 +421,27 @@ def run_qdd(args):
     U = inputs.gauge_field(W["L"], W["eps"], W["gauge_seed"])
     b = make_sources(W)
     nrhs = W["nrhs"]
-    g = qdd.qdd_create_gauge_field(ctx, W["L"], W["dom"], U)
+    # several ranks: the lattice is sharded in t (slabs of whole domains, strong
+    # scaling) when it splits into equal slabs of an even number of domain
+    # blocks; otherwise every rank solves its own copy (replicas)
+    shard, shard_reason = None, ""
+    if world > 1 and not args.replicas:
+        from paper_1502_04025_gb300 import dist as qdist
+
+        try:
+            shard = qdist.slab_partition(W["L"][3], W["dom"][3], world)[rank]
+        except ValueError as e:
+            shard_reason = str(e)
+    if shard is not None:
+        t0, lt = shard
+        comm = qdist.TorchComm(device=torch.device("cuda", local))
+        g = qdd.qdd_create_gauge_field_slab(ctx, qdist.local_lattice(W["L"], lt), W["dom"],
+                                            qdist.extended_links(U, W["L"], W["dom"], t0, lt), comm)
+        b = qdist.local_field(b, W["L"], t0, lt)
+        parallelism = f"t-slabs over {world} GPUs: {lt} planes each, face slots and boundary planes exchanged"
+    else:
+        g = qdd.qdd_create_gauge_field(ctx, W["L"], W["dom"], U)
+        parallelism = f"{world} replica(s)" + (f" ({shard_reason})" if world > 1 and not args.replicas else "")
     qdd.qdd_set_clover(g, W["csw"], W["kappa"])
     params = qdd.qdd_default_params(tol=W["tol"], restart_m=W["m"], nmr=W["nmr"], ncy=W["ncy"],
                                     sap_prec=W["sap_prec"], arnoldi_prec=W["arnoldi_prec"], max_restarts=200,
@@ -538,12 +563,12 @@ def run_qdd(args):
     e2e = {"value": statistics.mean(e2e_ms) if e2e_ms else None, "unit": "ms",
            "h2d_bytes_per_step": int(bh.nbytes), "d2h_bytes_per_step": int(xh.nbytes), "host_memory": "pinned"}
     parity = None
-    if rank == 0 and e2e_ms:
+    if rank == 0 and e2e_ms and shard is None:
         parity = sampled_residual(W, U, b, xh)
 
     # ---- batching: the same sources one at a time (the first source's solve, times nrhs)
     unbatched = None
-    if rank == 0 and nrhs > 1:
+    if rank == 0 and world == 1 and nrhs > 1:
         p1 = qdd.qdd_default_params(tol=W["tol"], restart_m=W["m"], nmr=W["nmr"], ncy=W["ncy"],
                                     sap_prec=W["sap_prec"], arnoldi_prec=W["arnoldi_prec"], max_restarts=200,
                                     nrhs=1, relax_eta=W.get("relax_eta", 0.0), reorth=W.get("reorth", 1))
@@ -566,7 +591,7 @@ def run_qdd(args):
     # Arnoldi operator): the plain FP64 GPU path the mixed-precision one is
     # measured against
     plain = None
-    if rank == 0 and args.config in (2, 4) and not args.no_fp64_compare:
+    if rank == 0 and world == 1 and args.config in (2, 4) and not args.no_fp64_compare:
         p64 = qdd.qdd_default_params(tol=W["tol"], restart_m=W["m"], nmr=W["nmr"], ncy=W["ncy"], sap_prec="f64",
                                      arnoldi_prec="f64", max_restarts=200, nrhs=nrhs, reorth=1)
         qdd.qdd_solve(g, bd, p64, x=xd, allow_noconv=True)
@@ -584,7 +609,7 @@ def run_qdd(args):
 
     # ---- full-lattice operator throughput (FP32 and FP16 storage) on a lattice > L2
     dslash = None
-    if not args.no_dslash and rank == 0 and args.config in (2, 4):
+    if not args.no_dslash and rank == 0 and world == 1 and args.config in (2, 4):
         Ud = inputs.gauge_field(DSL["L"], DSL["eps"], DSL["gauge_seed"])
         gd = qdd.qdd_create_gauge_field(ctx, DSL["L"], DSL["dom"], Ud)
         del Ud
@@ -629,7 +654,8 @@ def run_qdd(args):
     if rank == 0:
         last = reps[-1]
         line = {"metric": METRIC, "value": ms_step, "unit": "ms", "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False,
+                "scaling": "strong" if shard is not None else "weak",
                 "vs_baseline": None,
                 "dtype": ("f64" if W["sap_prec"] == "f64" else f"f64 outer / f32 arithmetic on {W['sap_prec']} "
                           "preconditioner storage"),
@@ -640,7 +666,7 @@ def run_qdd(args):
                            "sap_prec": W["sap_prec"], "arnoldi_prec": W["arnoldi_prec"],
                            "relax_eta": W.get("relax_eta", 0.0), "reorth": W.get("reorth", 1),
                            "l2": "256 MB buffer written before every step; Krylov working set larger than L2",
-                           "parallelism": f"{world} replica(s)"},
+                           "parallelism": parallelism},
                 "iters": last["iters"], "restarts": last["restarts"], "true_rel_res": last["true_rel_res"],
                 "converged": bool(last["converged"]),
                 "roofline": roof, "roofline_fp64_vector_algebra": blas_roof, "fma_peaks": fma,

@@ -53,7 +53,8 @@ typedef enum {
     QDD_ENAN = 5,     /* a NaN or Inf appeared in a residual */
     QDD_ETIMEOUT = 6, /* a bounded wait ran out (device flag or host poll) */
     QDD_ECUDA = 7,    /* a CUDA runtime call failed */
-    QDD_ENOTREADY = 8 /* serving: the ticket is still in flight */
+    QDD_ENOTREADY = 8, /* serving: the ticket is still in flight */
+    QDD_ECOMM = 9      /* a communication hook of a sharded gauge field failed */
 } qdd_status;
 
 /* Precision of the Schwarz preconditioner (arithmetic / storage), and of the
@@ -205,6 +206,17 @@ qdd_status qdd_set_link_compression(qdd_gauge *g, int two_rows);
 qdd_status qdd_link_compression(qdd_gauge *g, int *two_rows, int *is_su3);
 
 /*
+ * Form of the Schwarz block kernel (the result is the same bits either way):
+ * 0 (default) stages the domain's links and, when it fits, its clover in
+ * shared memory; 1 stages the links only, reads the clover through the
+ * cache and is compiled for three CTAs per SM (FP32 arithmetic on domains of
+ * at most 256 sites; otherwise form 0 runs).  The paper sizes its domains to
+ * the cache (Sec. 3.3); on the GPU the choice trades staged data against the
+ * number of domains an SM holds.
+ */
+qdd_status qdd_set_schwarz_variant(qdd_gauge *g, int variant);
+
+/*
  * Range-checked build (test aid; compute-sanitizer stands in elsewhere).
  * A library built with -DQDD_CHECK (libqdd_check.so) tests the indices of
  * the Schwarz kernel's stencil, face-slot and reduction accesses, of the
@@ -242,6 +254,69 @@ qdd_status qdd_set_clover(qdd_gauge *g, double c_sw, double kappa);
  * (A on even sites, A^{-1} on odd sites).  out: host pointer.
  */
 qdd_status qdd_get_clover(qdd_gauge *g, int which, double *out);
+
+/* ------------------------------------------------------ sharded lattices */
+
+/*
+ * Communication hooks of a lattice sharded over ranks (Sec. 3.6 of the paper
+ * distributes the lattice over processors and exchanges the boundaries).
+ * The caller implements them with its own communication library; every rank
+ * calls the collective entry points below in the same order.  Buffers are
+ * host memory owned by the library for the duration of the call.
+ *   allreduce_sum  buf[0..n) <- the sum over all ranks of buf[0..n) (doubles)
+ *   shift          cyclic shift along the rank ring: send to_up (bytes) to
+ *                  rank (rank+1) mod size and to_dn to (rank-1) mod size;
+ *                  receive from (rank-1) mod size into from_dn and from
+ *                  (rank+1) mod size into from_up (equal sizes everywhere;
+ *                  with size 1 a rank is its own neighbour both ways)
+ * Both return 0 on success; anything else aborts the call with QDD_ECOMM.
+ */
+typedef struct {
+    void *user;  /* passed back to the hooks */
+    int rank, size;
+    int (*allreduce_sum)(void *user, double *buf, size_t n);
+    int (*shift)(void *user, const void *to_up, void *from_dn, const void *to_dn, void *from_up, size_t bytes);
+} qdd_comm;
+
+/*
+ * A gauge field sharded in the time direction (Sec. 3.6: the lattice is
+ * split over processors, here into slabs of whole domains along t).  This
+ * rank owns the local lattice Lloc = (Lx, Ly, Lz, lt) at global times
+ * t0 .. t0+lt-1, with domains dom; lt/dom[3] must be even (>= 2) and t0 a
+ * multiple of 2*dom[3], so that the domain colouring is the global one.
+ * links_ext: the links of the extended local lattice (Lx, Ly, Lz,
+ * lt + 2*dom[3]) in the host layout, its first plane at global time
+ * t0 - dom[3] (periodic in the global lattice): the owned planes plus one
+ * domain block of halo on each side, which the clover term of the boundary
+ * planes needs.  comm: the rank's hooks (copied; `user` must stay valid
+ * until the gauge field is destroyed).  Spinors of every entry point are in
+ * the host layout of Lloc.  qdd_set_clover, qdd_apply_D (outputs F64, DF64,
+ * F32), qdd_sap_apply and qdd_solve (use_sap 0 or 1, no deflation) then act
+ * collectively: the Schwarz half-sweeps exchange the face slots that cross
+ * the slab boundaries (a cyclic shift after every half-sweep), the operator
+ * corrects its two boundary planes with the neighbours' hops, and the solver
+ * sums its dot products and norms over the ranks.  Other entry points treat
+ * the field as a periodic local lattice.
+ */
+qdd_status qdd_create_gauge_field_slab(qdd_ctx *ctx, const int Lloc[4], const int dom[4], const double *links_ext,
+                                       int links_on_device, const qdd_comm *comm, qdd_gauge **g);
+
+/*
+ * Host-only: the face slots a sharded lattice exchanges after a half-sweep
+ * of colour `colour` (the receiving domains have the other colour).
+ * out[0..2] = (first domain slot, domain count, direction) of the region
+ * sent to rank+1 (the first t-block's slots fed from below), out[3..5] the
+ * same for the region sent to rank-1 (the last t-block's slots fed from
+ * above); a direction's slots of domain d are face[d][k][foff[dir] ..
+ * foff[dir] + Vd/dom[3]) for the six components k.
+ */
+qdd_status qdd_slab_regions(const int Lloc[4], const int dom[4], int colour, int out[6]);
+
+/* Host-only: the face-slot layout of a domain shape: foff[8] the first slot
+ * of each direction (k = 2*mu + 0 forward, 1 backward hop of the receiving
+ * site), fcoord[Vd] the packed transverse index of each domain site (byte mu
+ * = the index of its coordinates transverse to mu); either may be NULL. */
+qdd_status qdd_layout_faces(const int L[4], const int dom[4], int foff[8], uint32_t *fcoord);
 
 /* ------------------------------------------------------------- operators */
 

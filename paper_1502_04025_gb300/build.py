@@ -20,7 +20,7 @@ LIB = os.path.join(HERE, "libqdd.so")
 # the range-checked variant (-DQDD_CHECK): test builds only
 BUILD_CHECK = os.path.join(HERE, "_build_check")
 LIB_CHECK = os.path.join(HERE, "libqdd_check.so")
-SOURCES = ["layout.cu", "clover.cu", "dslash.cu", "sap.cu", "blas.cu", "solver.cu", "api.cu", "serve.cu", "tune.cu", "mg.cu", "peak.cu"]
+SOURCES = ["layout.cu", "clover.cu", "dslash.cu", "sap.cu", "blas.cu", "solver.cu", "api.cu", "serve.cu", "tune.cu", "mg.cu", "peak.cu", "slab.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

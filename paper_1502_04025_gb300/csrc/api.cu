@@ -417,6 +417,40 @@ qdd_status qdd_create_gauge_field(qdd_ctx *ctx, const int L[4], const int dom[4]
     return QDD_OK;
 }
 
+qdd_status qdd_create_gauge_field_slab(qdd_ctx *ctx, const int Lloc[4], const int dom[4], const double *links_ext,
+                                       int links_on_device, const qdd_comm *comm, qdd_gauge **out)
+{
+    clear_error();
+    if (!ctx || !Lloc || !dom || !links_ext || !comm || !out) {
+        set_error("null argument");
+        return QDD_EINVAL;
+    }
+    *out = nullptr;
+    if (comm->size < 1 || comm->rank < 0 || comm->rank >= comm->size || !comm->allreduce_sum || !comm->shift) {
+        set_error("invalid communication hooks (rank %d of %d)", comm->rank, comm->size);
+        return QDD_EINVAL;
+    }
+    if (dom[3] < 2) {
+        set_error("invalid domain extent in t");
+        return QDD_EINVAL;
+    }
+    const int Le[4] = {Lloc[0], Lloc[1], Lloc[2], Lloc[3] + 2 * dom[3]};
+    const size_t Ls = (size_t)Lloc[0] * Lloc[1] * Lloc[2];
+    // the owned planes start dom[3] planes into the extended field (t is the slowest index)
+    const double *own = links_ext + (size_t)dom[3] * Ls * 4 * 18;
+    qdd_gauge *g = nullptr, *e = nullptr;
+    QDD_TRY(qdd_create_gauge_field(ctx, Lloc, dom, own, links_on_device, &g));
+    qdd_status st = qdd_create_gauge_field(ctx, Le, dom, links_ext, links_on_device, &e);
+    if (st == QDD_OK) st = slab_setup(g, e, *comm);
+    if (st != QDD_OK) {
+        if (!g->slab) qdd_destroy_gauge(e);
+        qdd_destroy_gauge(g);
+        return st;
+    }
+    *out = g;
+    return QDD_OK;
+}
+
 void qdd_destroy_gauge(qdd_gauge *g)
 {
     if (!g) return;
@@ -458,6 +492,18 @@ qdd_status qdd_check_hits(unsigned long long *hits)
 #endif
 }
 
+qdd_status qdd_set_schwarz_variant(qdd_gauge *g, int variant)
+{
+    clear_error();
+    if (!g || variant < 0 || variant > 1) {
+        set_error("invalid argument");
+        return QDD_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(g->mu);
+    g->sap_variant = variant;
+    return QDD_OK;
+}
+
 qdd_status qdd_check_set_wait_limit(int device, unsigned spins)
 {
     clear_error();
@@ -492,17 +538,27 @@ qdd_status qdd_set_clover(qdd_gauge *g, double c_sw, double kappa)
         set_error("c_sw and kappa must be finite");
         return QDD_EINVAL;
     }
+    // a sharded field takes the clover of its owned sites from its extended
+    // lattice, whose halo holds the links the boundary planes' leaves need
+    qdd_status ext_st = g->slab ? qdd_set_clover(g->slab->ext, c_sw, kappa) : QDD_OK;
     std::lock_guard<std::mutex> lk(g->mu);
     QDD_CUDA(cudaSetDevice(g->ctx->device));
     const size_t cb = (size_t)g->hg.V * 36 * sizeof(double2);
     QDD_TRY(g->clov64.ensure(g->ctx, cb));
     QDD_TRY(g->sclov64.ensure(g->ctx, cb));
-    DevMem flag;
-    QDD_TRY(flag.alloc(g->ctx, sizeof(int)));
-    QDD_CUDA(cudaMemset(flag.p, 0, sizeof(int)));
-    QDD_TRY(launch_clover_build(g, c_sw, kappa, flag.as<int>(), 0));
     int singular = 0;
-    QDD_CUDA(cudaMemcpy(&singular, flag.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (g->slab) {
+        g->have_clover = false;
+        if (ext_st != QDD_OK) return ext_st;
+        QDD_TRY(slab_clover_remap(g, 0));
+        QDD_CUDA(cudaDeviceSynchronize());
+    } else {
+        DevMem flag;
+        QDD_TRY(flag.alloc(g->ctx, sizeof(int)));
+        QDD_CUDA(cudaMemset(flag.p, 0, sizeof(int)));
+        QDD_TRY(launch_clover_build(g, c_sw, kappa, flag.as<int>(), 0));
+        QDD_CUDA(cudaMemcpy(&singular, flag.p, sizeof(int), cudaMemcpyDeviceToHost));
+    }
     g->ctx->timer.resolve();
     for (int p = 0; p < 5; p++) g->copies[p].valid = false;
     g->have_clover = false;
@@ -588,9 +644,17 @@ qdd_status qdd_apply_D(qdd_gauge *g, const double *in, double *out, int nrhs, qd
     QDD_TRY(launch_spinor_in(g, din, st->a.p, st->a_s.as<float>(), prec, nrhs, s));
     QDD_TRY(launch_dslash(g, arith, fp, st->a.p, st->a_s.as<float>(), prec, st->b.p, st->b_s.as<float>(), prec,
                           nullptr, nrhs, s));
-    QDD_TRY(stage_out(g, st->io, out, nrhs, on_device, s, &dout));
+    // a sharded field corrects the output's boundary planes from the input
+    // (FP64, host layout), so the host output must not reuse the input's staging
+    DevMem &oio = g->slab ? st->c : st->io;
+    if (g->slab && on_device && out == in) {
+        set_error("a sharded field needs separate input and output buffers");
+        return QDD_EINVAL;
+    }
+    QDD_TRY(stage_out(g, oio, out, nrhs, on_device, s, &dout));
     QDD_TRY(launch_spinor_out(g, st->b.p, st->b_s.as<float>(), dout, prec, nrhs, s));
-    return finish_out(g, st->io, out, nrhs, on_device, s);
+    QDD_TRY(slab_dslash_fix(g, din, false, (double2 *)dout, false, true, nrhs, s));
+    return finish_out(g, oio, out, nrhs, on_device, s);
 }
 
 qdd_status qdd_sap_apply(qdd_gauge *g, const double *eta, double *psi, double *rho, int nrhs, int nmr, int n_half,
@@ -624,9 +688,15 @@ qdd_status qdd_sap_apply(qdd_gauge *g, const double *eta, double *psi, double *r
     SapBuffers b{st->a.p, st->b.p, st->c.p, st->a_s.as<float>()};
     {
         SeqScope seq(g->ctx->timer, K_SAP, s);
-        for (int hs = 0; hs < n_half; hs++)
+        const bool sharded = g->slab != nullptr;
+        const size_t fesz = prec == QDD_PREC_F64 ? sizeof(double2) : sizeof(float2);
+        for (int hs = 0; hs < n_half; hs++) {
+            // a sharded field exchanges the face slots that cross the slab
+            // boundaries between half-sweeps, so no dependent launch there
             QDD_TRY(launch_sap_halfsweep(g, prec, b, hs & 1, nmr, nrhs, hs < 2, hs >= 1, 0, st->err.as<int>(), s,
-                                         hs >= 1, false));
+                                         hs >= 1 && !sharded, false));
+            if (sharded && (hs + 1 < n_half || rho)) QDD_TRY(slab_face_exchange(g, st->b.p, fesz, hs & 1, nrhs, s));
+        }
     }
     if (rho)  // bring the residual of the next colour up to date
         QDD_TRY(launch_sap_halfsweep(g, prec, b, n_half & 1, nmr, nrhs, 0, 1, 1, st->err.as<int>(), s));

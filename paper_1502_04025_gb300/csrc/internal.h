@@ -185,8 +185,26 @@ struct Workspace {
     }
 };
 
+// A gauge field sharded in t (qdd_create_gauge_field_slab): the rank's
+// communication hooks, the extended lattice whose clover term the owned
+// sites take, and the tables and buffers of the boundary exchanges.
+struct Slab {
+    qdd_comm comm{};
+    int lt = 0, Ls = 0;        // local t extent, sites of one t plane
+    qdd_gauge *ext = nullptr;  // (Lx, Ly, Lz, lt + 2 dom_t): one domain block of halo on each side
+    DevMem ext_map;            // [V] internal index in ext of each owned site (clover remap)
+    DevMem plane_base;         // [2][Ls] int64: internal element offset of component 0, planes 0 and lt-1
+    DevMem last_link;          // [Ls] int64: element offset of U_t at plane lt-1 in the FP64 links
+    DevMem bufs;               // [4][nrhs][Ls][6] double2: own backward push, own forward projection, received
+    size_t buf_rhs = 0;
+    void *host = nullptr;      // pinned staging of the cyclic shifts
+    size_t host_bytes = 0;
+    ~Slab();
+};
+
 struct Gauge {
     Ctx *ctx = nullptr;
+    std::unique_ptr<Slab> slab;  // set for a field sharded in t
     HostGeom hg;
     Geom geom{};
     DevMem d_nbl, d_nbd, d_site_of, d_block_slot, d_fcoord;
@@ -194,6 +212,7 @@ struct Gauge {
     bool su3 = false;         // every link SU(3) to kSu3Tol
     bool two_rows = false;    // the FP32/16-bit full-lattice operator reads two rows per link
     bool have_clover = false;
+    int sap_variant = 0;      // Schwarz kernel form (qdd_set_schwarz_variant)
     double csw = 0, kappa = 0;
     DevMem clov64, sclov64;   // FP64 clover A and Schwarz form (A even, A^-1 odd)
     PrecCopy copies[5];       // index = qdd_prec; F64 entry aliases the masters
@@ -313,6 +332,24 @@ qdd_status blas_combine(Ctx *ctx, const void *src, bool src_f32, int nsrc, int64
 // precision of the multigrid's Schwarz smoother
 qdd_status mg_vcycle(Gauge *g, const double2 *v, void *z, qdd_prec zp, cudaStream_t s);
 qdd_prec mg_smoother_prec(const Gauge *g);
+
+// slab.cu: the exchanges of a field sharded in t (no-ops without a slab)
+// sum n doubles of host memory over the ranks
+qdd_status slab_allreduce(Gauge *g, double *host, size_t n);
+// sum n complex values of device memory over the ranks (in place; synchronises s)
+qdd_status slab_allreduce_dev(Gauge *g, double2 *dev, int n, cudaStream_t s);
+// after a Schwarz half-sweep of colour `colour`: the face slots that cross the
+// slab boundaries move to the neighbouring ranks (esz bytes per slot element)
+qdd_status slab_face_exchange(Gauge *g, void *face, size_t esz, int colour, int nrhs, cudaStream_t s);
+// out (FP64, internal layout or, host_layout, the host layout) holds D in, or
+// b - D in when residual; replace the hops across the slab boundaries that
+// the local periodic wrap took with the neighbours' (in FP64 or FP32)
+qdd_status slab_dslash_fix(Gauge *g, const void *in, bool in_f32, double2 *out, bool residual, bool host_layout,
+                           int nrhs, cudaStream_t s);
+// the clover of the owned sites from the extended lattice (after its build)
+qdd_status slab_clover_remap(Gauge *g, cudaStream_t s);
+qdd_status slab_setup(Gauge *g, qdd_gauge *ext, const qdd_comm &comm);
+void slab_regions(const HostGeom &hg, int colour, int out[6]);
 
 // solver.cu
 std::unique_ptr<Workspace> make_workspace();

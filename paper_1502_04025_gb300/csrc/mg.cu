@@ -815,6 +815,10 @@ qdd_status qdd_mg_setup(qdd_gauge *g, const qdd_mg_params *p, const double *w0, 
         set_error("set_clover has not been called");
         return QDD_EINVAL;
     }
+    if (g->slab) {
+        set_error("the multigrid preconditioner is built on unsharded gauge fields only");
+        return QDD_EINVAL;
+    }
     std::lock_guard<std::mutex> lk(g->mu);
     Ctx *ctx = g->ctx;
     QDD_CUDA(cudaSetDevice(ctx->device));

@@ -376,8 +376,12 @@ enum SapPhase : int {
     PH_RECON_ODD = 4    // x_o = A_oo^{-1} (rho_o + kappa H_oe x_e)
 };
 
-template <typename R, typename SL, typename SC, typename SS, typename SP, bool STL, bool STC>
-__global__ void __launch_bounds__(256) k_sap(const SapArgs<R, SL, SC, SS, SP> a)
+// MAXT / MINB: the launch bounds.  The default form allows 256 threads (an
+// 8x4^3 domain); the occupancy form (128 threads, 3 CTAs per SM) caps the
+// registers at 170 so that three 4^4 domains run on an SM at once.
+template <typename R, typename SL, typename SC, typename SS, typename SP, bool STL, bool STC, int MAXT = 256,
+          int MINB = 1>
+__global__ void __launch_bounds__(MAXT, MINB) k_sap(const SapArgs<R, SL, SC, SS, SP> a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     const Geom &g = a.g;
@@ -742,15 +746,19 @@ __global__ void __launch_bounds__(128) k_sap_face_apply(const Geom g, const Fiel
 
 // ---------------------------------------------------------------- launch
 
-template <typename R, typename SL, typename SC, typename SS, typename SP, bool STL, bool STC>
+template <typename R, typename SL, typename SC, typename SS, typename SP, bool STL, bool STC, int MAXT = 256,
+          int MINB = 1>
 static qdd_status run_sap(Gauge *g, const SapArgs<R, SL, SC, SS, SP> &a, cudaStream_t s, bool pdl, bool timed)
 {
     const HostGeom &hg = g->hg;
     size_t smem = sap_smem_layout<R, SL, SC>(hg.Vd, STL, STC);
-    auto kern = k_sap<R, SL, SC, SS, SP, STL, STC>;
+    auto kern = k_sap<R, SL, SC, SS, SP, STL, STC, MAXT, MINB>;
     static thread_local size_t configured = 0;
     if (configured < smem) {
         QDD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        if (MINB > 1)  // room for MINB CTAs' shared memory on an SM
+            QDD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                          (int)cudaSharedmemCarveoutMaxShared));
         configured = smem;
     }
     cudaLaunchConfig_t cfg = {};
@@ -780,6 +788,18 @@ static size_t smem_limit()
     return lim;
 }
 
+static size_t smem_per_sm()
+{
+    static size_t lim = 0;
+    if (!lim) {
+        int dev = 0, v = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        lim = (size_t)v;
+    }
+    return lim;
+}
+
 // Links are staged in shared memory, then the Schwarz clover when it fits too.
 template <typename R, typename SL, typename SC, typename SS, typename SP>
 static qdd_status dispatch_staging(Gauge *g, const SapArgs<R, SL, SC, SS, SP> &a, cudaStream_t s, bool pdl,
@@ -796,6 +816,13 @@ static qdd_status dispatch_staging(Gauge *g, const SapArgs<R, SL, SC, SS, SP> &a
     }
     const int Vd = hg.Vd;
     const size_t lim = smem_limit() - 128;  // the kernel's static shared memory
+    // the occupancy form: links staged, clover read through the cache, three
+    // CTAs per SM (FP32 arithmetic, domains of at most 256 sites)
+    if constexpr (sizeof(R) == 4) {
+        if (g->sap_variant == 1 && hg.Vh <= 128 && 3 * (sap_smem_layout<R, SL, SC>(Vd, true, false) + 128) <= 3 * lim &&
+            3 * (sap_smem_layout<R, SL, SC>(Vd, true, false) + 1024) <= smem_per_sm())
+            return run_sap<R, SL, SC, SS, SP, true, false, 128, 3>(g, a, s, pdl, timed);
+    }
     if (sap_smem_layout<R, SL, SC>(Vd, true, true) <= lim)
         return run_sap<R, SL, SC, SS, SP, true, true>(g, a, s, pdl, timed);
     if (sap_smem_layout<R, SL, SC>(Vd, true, false) <= lim)

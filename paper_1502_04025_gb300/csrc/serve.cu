@@ -224,6 +224,10 @@ qdd_status qdd_submit(qdd_ctx *ctx, qdd_gauge *g, const double *b, double *x, co
         set_error("set_clover has not been called");
         return QDD_EINVAL;
     }
+    if (g->slab) {
+        set_error("a sharded gauge field is solved collectively with qdd_solve, not queued");
+        return QDD_EINVAL;
+    }
     auto r = std::make_shared<Request>();
     r->g = g;
     r->b.assign(b, b + (size_t)g->hg.V * 24 * p->nrhs);

@@ -158,6 +158,11 @@ qdd_status solve_impl(Gauge *g, Workspace *wsp, const double *b_in, double *x_ou
         set_error("set_clover has not been called");
         return QDD_EINVAL;
     }
+    if (g->slab && (p->use_sap == 2 || p->dr_k > 0)) {
+        set_error("a sharded gauge field solves with the Schwarz preconditioner or none, without deflation");
+        return QDD_EINVAL;
+    }
+    const bool sharded = g->slab != nullptr;
     // the preconditioner's storage (the multigrid smoother's, when it is used)
     const qdd_prec sp = p->use_sap == 2 ? mg_smoother_prec(g) : p->sap_prec;
     const qdd_prec zp = sp == QDD_PREC_F64 ? QDD_PREC_F64 : QDD_PREC_F32;
@@ -200,6 +205,7 @@ qdd_status solve_impl(Gauge *g, Workspace *wsp, const double *b_in, double *x_ou
     for (int r = 0; r < B; r++) QDD_TRY(blas_norm2(ctx, Bv + r * n, n, dev + sm.bnrm() + r, scr, s));
     QDD_CUDA(cudaMemcpyAsync(host + sm.bnrm(), dev + sm.bnrm(), B * sizeof(double2), cudaMemcpyDeviceToHost, s));
     QDD_CUDA(cudaStreamSynchronize(s));
+    QDD_TRY(slab_allreduce(g, (double *)(host + sm.bnrm()), 2 * (size_t)B));  // sharded: over the ranks
     std::vector<double> bnorm(B);
     for (int r = 0; r < B; r++) bnorm[r] = std::sqrt(host[sm.bnrm() + r].x);
 
@@ -228,11 +234,14 @@ qdd_status solve_impl(Gauge *g, Workspace *wsp, const double *b_in, double *x_ou
         // ---- true residual into V_0 (FP64)
         if (cycle == 0)
             QDD_CUDA(cudaMemcpyAsync(V, Bv, (size_t)n * 16 * B, cudaMemcpyDeviceToDevice, s));
-        else
+        else {
             QDD_TRY(launch_dslash(g, QDD_PREC_F64, QDD_PREC_F64, X, nullptr, QDD_PREC_F64, pending_dr ? w.Vt.as<double2>() : V,
                                   nullptr, QDD_PREC_F64, Bv, B, s));
+            QDD_TRY(slab_dslash_fix(g, X, false, V, true, false, B, s));
+        }
         double2 *R0 = (cycle > 0 && pending_dr) ? w.Vt.as<double2>() : V;
         for (int r = 0; r < B; r++) QDD_TRY(blas_norm2(ctx, R0 + r * n, n, dev + sm.nrm1() + r, scr, s));
+        QDD_TRY(slab_allreduce_dev(g, dev + sm.nrm1(), B, s));
         QDD_CUDA(cudaMemcpyAsync(host + sm.nrm1(), dev + sm.nrm1(), B * sizeof(double2), cudaMemcpyDeviceToHost, s));
         QDD_CUDA(cudaStreamSynchronize(s));
         bool all = true;
@@ -393,9 +402,14 @@ qdd_status solve_impl(Gauge *g, Workspace *wsp, const double *b_in, double *x_ou
                 rho_ready = false;
                 sb.psi = zj;
                 SeqScope seq(ctx->timer, K_SAP, s);
-                for (int hs = 0; hs < 2 * p->ncy; hs++)
+                const size_t fesz = sp == QDD_PREC_F64 ? sizeof(double2) : sizeof(float2);
+                for (int hs = 0; hs < 2 * p->ncy; hs++) {
+                    // sharded: the face slots crossing the slab boundaries move
+                    // between half-sweeps (no dependent launch across them)
                     QDD_TRY(launch_sap_halfsweep(g, sp, sb, hs & 1, p->nmr, B, hs < 2, hs >= 1, 0, w.err.as<int>(), s,
-                                                 hs >= 1, false));
+                                                 hs >= 1 && !sharded, false));
+                    if (sharded && hs + 1 < 2 * p->ncy) QDD_TRY(slab_face_exchange(g, w.face.p, fesz, hs & 1, B, s));
+                }
             } else {
                 QDD_TRY(launch_spinor_convert(g, vj, nullptr, QDD_PREC_F64, zj, nullptr, zp, B, s));
             }
@@ -415,13 +429,16 @@ qdd_status solve_impl(Gauge *g, Workspace *wsp, const double *b_in, double *x_ou
             else
                 QDD_TRY(launch_dslash(g, QDD_PREC_F32, QDD_PREC_F32, zj, nullptr, QDD_PREC_F32, wv, nullptr,
                                       QDD_PREC_F64, nullptr, B, s));
+            QDD_TRY(slab_dslash_fix(g, zj, zp == QDD_PREC_F32, wv, false, false, B, s));
             // classical Gram-Schmidt, pass 1 (dots include <w, w>)
             for (int r = 0; r < B; r++) {
                 if (!open[r]) continue;
                 double2 *d1 = dev + sm.dots1() + (size_t)r * (m + 2);
                 QDD_TRY(blas_cdot_multi(ctx, V + r * n, j + 2, ldV, wv + r * n, n, d1, scr, s));
+                QDD_TRY(slab_allreduce_dev(g, d1, j + 2, s));  // sharded: sums over the ranks
                 QDD_TRY(blas_caxpy_multi_norm(ctx, V + r * n, j + 1, ldV, d1, wv + r * n, n, dev + sm.nrm1() + r,
                                               scr, s));
+                QDD_TRY(slab_allreduce_dev(g, dev + sm.nrm1() + r, 1, s));
             }
             std::vector<char> two(B, 0);
             if (p->reorth == 2) {
@@ -429,8 +446,10 @@ qdd_status solve_impl(Gauge *g, Workspace *wsp, const double *b_in, double *x_ou
                     if (!open[r]) continue;
                     double2 *d2 = dev + sm.dots2() + (size_t)r * (m + 2);
                     QDD_TRY(blas_cdot_multi(ctx, V + r * n, j + 1, ldV, wv + r * n, n, d2, scr, s));
+                    QDD_TRY(slab_allreduce_dev(g, d2, j + 1, s));
                     QDD_TRY(blas_caxpy_multi_norm(ctx, V + r * n, j + 1, ldV, d2, wv + r * n, n,
                                                   dev + sm.nrm2() + r, scr, s));
+                    QDD_TRY(slab_allreduce_dev(g, dev + sm.nrm2() + r, 1, s));
                     two[r] = 1;
                 }
             }
@@ -447,8 +466,10 @@ qdd_status solve_impl(Gauge *g, Workspace *wsp, const double *b_in, double *x_ou
                         any = true;
                         double2 *d2 = dev + sm.dots2() + (size_t)r * (m + 2);
                         QDD_TRY(blas_cdot_multi(ctx, V + r * n, j + 1, ldV, wv + r * n, n, d2, scr, s));
+                        QDD_TRY(slab_allreduce_dev(g, d2, j + 1, s));
                         QDD_TRY(blas_caxpy_multi_norm(ctx, V + r * n, j + 1, ldV, d2, wv + r * n, n,
                                                       dev + sm.nrm2() + r, scr, s));
+                        QDD_TRY(slab_allreduce_dev(g, dev + sm.nrm2() + r, 1, s));
                     }
                 }
                 if (any) {

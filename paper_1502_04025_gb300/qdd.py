@@ -19,12 +19,13 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 # QDD_CHECKED=1 loads the range-checked build of the same library (tests)
 LIB_PATH = os.path.join(HERE, "libqdd_check.so" if os.environ.get("QDD_CHECKED") == "1" else "libqdd.so")
 
-QDD_OK, QDD_EINVAL, QDD_ENOMEM, QDD_EBUDGET, QDD_ENOCONV, QDD_ENAN, QDD_ETIMEOUT, QDD_ECUDA, QDD_ENOTREADY = range(9)
+(QDD_OK, QDD_EINVAL, QDD_ENOMEM, QDD_EBUDGET, QDD_ENOCONV, QDD_ENAN, QDD_ETIMEOUT, QDD_ECUDA, QDD_ENOTREADY,
+ QDD_ECOMM) = range(10)
 QDD_PREC_F64, QDD_PREC_F32, QDD_PREC_F16S, QDD_PREC_BF16S, QDD_PREC_DF64, QDD_PREC_H16 = range(6)
 PRECS = {"f64": QDD_PREC_F64, "f32": QDD_PREC_F32, "f16": QDD_PREC_F16S, "bf16": QDD_PREC_BF16S,
          "df64": QDD_PREC_DF64, "h16": QDD_PREC_H16}
 STATUS_NAMES = ["QDD_OK", "QDD_EINVAL", "QDD_ENOMEM", "QDD_EBUDGET", "QDD_ENOCONV", "QDD_ENAN", "QDD_ETIMEOUT",
-                "QDD_ECUDA", "QDD_ENOTREADY"]
+                "QDD_ECUDA", "QDD_ENOTREADY", "QDD_ECOMM"]
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{os.path.basename(LIB_PATH)} is not built ({LIB_PATH}); run __graft_entry__.build()")
@@ -64,6 +65,16 @@ class qdd_tune_result(ctypes.Structure):
 
 
 _vp = ctypes.c_void_p
+
+# communication hooks of a sharded lattice (qdd_comm)
+ALLREDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_size_t)
+SHIFT_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                            ctypes.c_void_p, ctypes.c_size_t)
+
+
+class qdd_comm(ctypes.Structure):
+    _fields_ = [("user", ctypes.c_void_p), ("rank", ctypes.c_int), ("size", ctypes.c_int),
+                ("allreduce_sum", ALLREDUCE_FN), ("shift", SHIFT_FN)]
 _ip = ctypes.POINTER(ctypes.c_int)
 _dp = ctypes.POINTER(ctypes.c_double)
 
@@ -79,10 +90,15 @@ _SIGS = {
     "qdd_measure_fma_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp, _dp]),
     "qdd_create_gauge_field": (ctypes.c_int, [_vp, _ip, _ip, _vp, ctypes.c_int, ctypes.POINTER(_vp)]),
     "qdd_destroy_gauge": (None, [_vp]),
+    "qdd_create_gauge_field_slab": (ctypes.c_int, [_vp, _ip, _ip, _vp, ctypes.c_int, ctypes.POINTER(qdd_comm),
+                                                   ctypes.POINTER(_vp)]),
+    "qdd_slab_regions": (ctypes.c_int, [_ip, _ip, ctypes.c_int, _ip]),
+    "qdd_layout_faces": (ctypes.c_int, [_ip, _ip, _ip, _vp]),
     "qdd_set_link_compression": (ctypes.c_int, [_vp, ctypes.c_int]),
     "qdd_link_compression": (ctypes.c_int, [_vp, _ip, _ip]),
     "qdd_check_hits": (ctypes.c_int, [ctypes.POINTER(ctypes.c_ulonglong)]),
     "qdd_check_set_wait_limit": (ctypes.c_int, [ctypes.c_int, ctypes.c_uint]),
+    "qdd_set_schwarz_variant": (ctypes.c_int, [_vp, ctypes.c_int]),
     "qdd_set_clover": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double]),
     "qdd_get_clover": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
     "qdd_apply_D": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp]),
@@ -233,8 +249,43 @@ def qdd_create_gauge_field(ctx, L, dom, links):
     return h
 
 
+# the hooks of each sharded gauge field, kept alive until it is destroyed
+_slab_hooks = {}
+
+
+def qdd_create_gauge_field_slab(ctx, Lloc, dom, links_ext, comm):
+    """A gauge field sharded in t: this rank's local lattice Lloc, the links of
+    the extended local lattice (one domain block of halo on each side) and
+    the communication hooks (an object with a ``struct`` qdd_comm field, kept
+    alive here until the field is destroyed)."""
+    h = _vp()
+    p, dev = _ptr(links_ext)
+    _check(_lib.qdd_create_gauge_field_slab(ctx, _ivec(Lloc), _ivec(dom), p, dev, ctypes.byref(comm.struct),
+                                            ctypes.byref(h)), "qdd_create_gauge_field_slab")
+    _slab_hooks[h.value] = comm
+    return h
+
+
+def qdd_slab_regions(Lloc, dom, colour: int):
+    """((first domain slot, domains, direction) sent up, (...) sent down) of the
+    face slots exchanged after a half-sweep of `colour` (host logic)."""
+    out = (ctypes.c_int * 6)()
+    _check(_lib.qdd_slab_regions(_ivec(Lloc), _ivec(dom), int(colour), out), "qdd_slab_regions")
+    return tuple(out[0:3]), tuple(out[3:6])
+
+
+def qdd_layout_faces(L, dom):
+    """(foff[8], fcoord[Vd]) of the face-slot layout of a domain shape (host logic)."""
+    Vd = int(np.prod(dom))
+    foff = (ctypes.c_int * 8)()
+    fcoord = np.zeros(Vd, dtype=np.uint32)
+    _check(_lib.qdd_layout_faces(_ivec(L), _ivec(dom), foff, fcoord.ctypes.data), "qdd_layout_faces")
+    return list(foff), fcoord
+
+
 def qdd_destroy_gauge(g):
     _lib.qdd_destroy_gauge(g)
+    _slab_hooks.pop(g.value if isinstance(g, _vp) else g, None)
 
 
 def qdd_set_link_compression(g, two_rows: bool):
@@ -255,6 +306,12 @@ def qdd_check_hits() -> int:
     h = ctypes.c_ulonglong()
     _check(_lib.qdd_check_hits(ctypes.byref(h)), "qdd_check_hits")
     return h.value
+
+
+def qdd_set_schwarz_variant(g, variant: int):
+    """0: links and clover staged when they fit; 1: links staged, clover
+    through the cache, three CTAs per SM (same results)."""
+    _check(_lib.qdd_set_schwarz_variant(g, int(variant)), "qdd_set_schwarz_variant")
 
 
 def qdd_check_set_wait_limit(device: int, spins: int):
