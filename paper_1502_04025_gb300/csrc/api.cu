@@ -642,6 +642,8 @@ qdd_status qdd_apply_D(qdd_gauge *g, const double *in, double *out, int nrhs, qd
         QDD_TRY(st->b_s.ensure(g->ctx, V * 4 * nrhs));
     }
     QDD_TRY(launch_spinor_in(g, din, st->a.p, st->a_s.as<float>(), prec, nrhs, s));
+    // a sharded field: its boundary planes (FP64, host layout) move while the operator runs
+    QDD_TRY(slab_dslash_begin(g, din, false, true, nrhs, s));
     QDD_TRY(launch_dslash(g, arith, fp, st->a.p, st->a_s.as<float>(), prec, st->b.p, st->b_s.as<float>(), prec,
                           nullptr, nrhs, s));
     // a sharded field corrects the output's boundary planes from the input
@@ -653,7 +655,7 @@ qdd_status qdd_apply_D(qdd_gauge *g, const double *in, double *out, int nrhs, qd
     }
     QDD_TRY(stage_out(g, oio, out, nrhs, on_device, s, &dout));
     QDD_TRY(launch_spinor_out(g, st->b.p, st->b_s.as<float>(), dout, prec, nrhs, s));
-    QDD_TRY(slab_dslash_fix(g, din, false, (double2 *)dout, false, true, nrhs, s));
+    QDD_TRY(slab_dslash_end(g, (double2 *)dout, false, nrhs, s));
     return finish_out(g, oio, out, nrhs, on_device, s);
 }
 
@@ -688,14 +690,15 @@ qdd_status qdd_sap_apply(qdd_gauge *g, const double *eta, double *psi, double *r
     SapBuffers b{st->a.p, st->b.p, st->c.p, st->a_s.as<float>()};
     {
         SeqScope seq(g->ctx->timer, K_SAP, s);
-        const bool sharded = g->slab != nullptr;
-        const size_t fesz = prec == QDD_PREC_F64 ? sizeof(double2) : sizeof(float2);
         for (int hs = 0; hs < n_half; hs++) {
-            // a sharded field exchanges the face slots that cross the slab
-            // boundaries between half-sweeps, so no dependent launch there
-            QDD_TRY(launch_sap_halfsweep(g, prec, b, hs & 1, nmr, nrhs, hs < 2, hs >= 1, 0, st->err.as<int>(), s,
-                                         hs >= 1 && !sharded, false));
-            if (sharded && (hs + 1 < n_half || rho)) QDD_TRY(slab_face_exchange(g, st->b.p, fesz, hs & 1, nrhs, s));
+            // a sharded field exchanges the face slots that cross its slab
+            // boundaries while the interior domains are swept
+            if (g->slab)
+                QDD_TRY(slab_sap_halfsweep(g, prec, b, hs & 1, nmr, nrhs, hs < 2, hs >= 1, st->err.as<int>(), s,
+                                           hs + 1 < n_half || rho));
+            else
+                QDD_TRY(launch_sap_halfsweep(g, prec, b, hs & 1, nmr, nrhs, hs < 2, hs >= 1, 0, st->err.as<int>(), s,
+                                             hs >= 1, false));
         }
     }
     if (rho)  // bring the residual of the next colour up to date

@@ -197,8 +197,13 @@ struct Slab {
     DevMem last_link;          // [Ls] int64: element offset of U_t at plane lt-1 in the FP64 links
     DevMem bufs;               // [4][nrhs][Ls][6] double2: own backward push, own forward projection, received
     size_t buf_rhs = 0;
-    void *host = nullptr;      // pinned staging of the cyclic shifts
-    size_t host_bytes = 0;
+    // page-locked staging of the cyclic shifts: face slots, operator planes, sums
+    void *host_face = nullptr, *host_op = nullptr, *host_red = nullptr;
+    size_t face_bytes = 0, op_bytes = 0, red_bytes = 0;
+    // the exchanges run on a side stream while the interior computes
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    bool op_host_layout = false;  // the pending operator exchange's addressing
     ~Slab();
 };
 
@@ -302,9 +307,11 @@ unsigned long long check_hits_sap();
 qdd_status set_first_wait_spins_sap(unsigned spins);
 unsigned long long check_hits_dslash();
 unsigned long long check_hits_mg();
+// part: 0 every domain of the colour; 1 those of the first and last t-block
+// (a sharded field's boundary), 2 the others
 qdd_status launch_sap_halfsweep(Gauge *g, qdd_prec prec, const SapBuffers &b, int colour, int nmr, int nrhs,
                                 int first_psi, int gather, int gather_only, int *d_err, cudaStream_t s,
-                                bool pdl = false, bool timed = true);
+                                bool pdl = false, bool timed = true, int part = 0);
 size_t sap_smem_bytes(const HostGeom &hg, qdd_prec prec, bool stage_links, bool stage_clover);
 
 // blas.cu (FP64 complex vectors of n elements, stored as double2; scratch holds
@@ -338,14 +345,20 @@ qdd_prec mg_smoother_prec(const Gauge *g);
 qdd_status slab_allreduce(Gauge *g, double *host, size_t n);
 // sum n complex values of device memory over the ranks (in place; synchronises s)
 qdd_status slab_allreduce_dev(Gauge *g, double2 *dev, int n, cudaStream_t s);
-// after a Schwarz half-sweep of colour `colour`: the face slots that cross the
-// slab boundaries move to the neighbouring ranks (esz bytes per slot element)
-qdd_status slab_face_exchange(Gauge *g, void *face, size_t esz, int colour, int nrhs, cudaStream_t s);
-// out (FP64, internal layout or, host_layout, the host layout) holds D in, or
-// b - D in when residual; replace the hops across the slab boundaries that
-// the local periodic wrap took with the neighbours' (in FP64 or FP32)
-qdd_status slab_dslash_fix(Gauge *g, const void *in, bool in_f32, double2 *out, bool residual, bool host_layout,
-                           int nrhs, cudaStream_t s);
+// One Schwarz half-sweep of a sharded field, in the overlap order of Sec. 3.6:
+// the domains of the first and last t-block first, then the interior, while
+// the face slots the boundary domains pushed across the slab boundaries move
+// to the neighbouring ranks on the side stream (when exchange is set); the
+// next work on s waits for the received slots.
+qdd_status slab_sap_halfsweep(Gauge *g, qdd_prec prec, const SapBuffers &b, int colour, int nmr, int nrhs,
+                              int first_psi, int gather, int *d_err, cudaStream_t s, bool exchange);
+// The operator on a sharded field: begin before the operator's launch (packs
+// the boundary planes of in, FP64 or FP32, internal or host layout, on the
+// side stream), end after it (the cyclic shift runs while the operator
+// computes; then out, FP64 in the same layout, holding D in, or b - D in when
+// residual, gets the neighbours' hops in place of the wrapped ones).
+qdd_status slab_dslash_begin(Gauge *g, const void *in, bool in_f32, bool host_layout, int nrhs, cudaStream_t s);
+qdd_status slab_dslash_end(Gauge *g, double2 *out, bool residual, int nrhs, cudaStream_t s);
 // the clover of the owned sites from the extended lattice (after its build)
 qdd_status slab_clover_remap(Gauge *g, cudaStream_t s);
 qdd_status slab_setup(Gauge *g, qdd_gauge *ext, const qdd_comm &comm);

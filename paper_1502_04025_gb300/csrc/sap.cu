@@ -141,6 +141,11 @@ struct SapArgs {
     R kappa;
     int colour, nmr, nrhs, first_psi, gather;
     int *err;
+    // the domains of this launch: block b sweeps domain colour*Nd/2 + dfirst +
+    // (b < nsplit ? b : b + dskip); one launch over all of a colour's
+    // domains is (0, grid, 0); a sharded field sweeps its boundary t-blocks
+    // first and its interior second
+    int dfirst, nsplit, dskip, nblocks;  // nblocks: the grid
 };
 
 __host__ __device__ constexpr size_t align128(size_t b) { return (b + 127) & ~(size_t)127; }
@@ -178,29 +183,28 @@ struct SapBlock {
         }
     }
 
-    // out = C(s) in : the Schwarz clover of this domain's site s, both blocks
+    // out = C(s) in : the Schwarz clover of this domain's site s, both blocks;
+    // a 16-bit clover's per-site scale multiplies the 12 products, not the 36
+    // stored entries
     __device__ __forceinline__ void clover(int s, const cpx<R> *in, cpx<R> *out) const
     {
 #pragma unroll
         for (int blk = 0; blk < 2; blk++) {
             cpx<R> m[18];
             if (STC) {
-                R sc = SC::kScaled ? (R)sCs[s] : (R)1;
 #pragma unroll
-                for (int k = 0; k < 18; k++) {
-                    cpx<R> v = ld_s<R>(sC + (blk * 18 + k) * Vd + s);
-                    m[k] = SC::kScaled ? sc * v : v;
-                }
+                for (int k = 0; k < 18; k++) m[k] = ld_s<R>(sC + (blk * 18 + k) * Vd + s);
             } else {
                 const typename SC::T2 *p = a.C.p + ((int64_t)d * 36 + blk * 18) * Vd + s;
-                R sc = SC::kScaled ? (R)__ldg(a.C.scale + (int64_t)d * Vd + s) : (R)1;
 #pragma unroll
-                for (int k = 0; k < 18; k++) {
-                    cpx<R> v = ld_c<R>(p + (int64_t)k * Vd);
-                    m[k] = SC::kScaled ? sc * v : v;
-                }
+                for (int k = 0; k < 18; k++) m[k] = ld_c<R>(p + (int64_t)k * Vd);
             }
             herm6_mul(m, in + 6 * blk, out + 6 * blk);
+        }
+        if (SC::kScaled) {
+            const R sc = STC ? (R)sCs[s] : (R)__ldg(a.C.scale + (int64_t)d * Vd + s);
+#pragma unroll
+            for (int k = 0; k < 12; k++) out[k] = sc * out[k];
         }
     }
 
@@ -387,7 +391,8 @@ __global__ void __launch_bounds__(MAXT, MINB) k_sap(const SapArgs<R, SL, SC, SS,
     const Geom &g = a.g;
     const int Vd = g.Vd, Vh = g.Vh;
     const int i = threadIdx.x;
-    const int d = a.colour * g.Nd2 + blockIdx.x;
+    const int bx = blockIdx.x;
+    const int d = a.colour * g.Nd2 + a.dfirst + (bx < a.nsplit ? bx : bx + a.dskip);
     const int se = i, so = Vh + i;
 
     unsigned char *ptr = smem;
@@ -762,7 +767,7 @@ static qdd_status run_sap(Gauge *g, const SapArgs<R, SL, SC, SS, SP> &a, cudaStr
         configured = smem;
     }
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(hg.Nd2);
+    cfg.gridDim = dim3(a.nblocks);
     cfg.blockDim = dim3(hg.Vh);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
@@ -878,31 +883,38 @@ size_t sap_smem_bytes(const HostGeom &hg, qdd_prec prec, bool stl, bool stc)
 
 qdd_status launch_sap_halfsweep(Gauge *g, qdd_prec prec, const SapBuffers &b, int colour, int nmr, int nrhs,
                                 int first_psi, int gather, int gather_only, int *d_err, cudaStream_t s, bool pdl,
-                                bool timed)
+                                bool timed, int part)
 {
     QDD_TRY(ensure_copy(g, prec, s));
     const int64_t rs = (int64_t)g->hg.V * 12, ss = g->hg.V, fs = (int64_t)g->hg.Nd * 6 * g->hg.nf;
+    // part 1: the first and last t-block's domains of the colour; part 2: the others
+    const int half = g->hg.nb[0] * g->hg.nb[1] * g->hg.nb[2] / 2, nd2 = g->hg.Nd2;
+    const int dfirst = part == 2 ? half : 0;
+    const int nsplit = part == 1 ? half : (part == 2 ? nd2 - 2 * half : nd2);
+    const int dskip = part == 1 ? nd2 - 2 * half : 0;
+    const int nblocks = part == 1 ? 2 * half : nsplit;
+    if (nblocks == 0) return QDD_OK;  // a slab of two t-blocks has no interior
     PrecCopy &c = g->copies[prec];
     switch (prec) {
     case QDD_PREC_F64: {
         SapArgs<double, StF64, StF64, StF64, StF64> a{
             g->geom, {g->links64.as<double2>(), nullptr}, {g->sclov64.as<double2>(), nullptr},
             {(double2 *)b.rho, nullptr}, (cpx<double> *)b.face, {(double2 *)b.psi, nullptr},
-            rs, ss, fs, g->kappa, colour, nmr, nrhs, first_psi, gather, d_err};
+            rs, ss, fs, g->kappa, colour, nmr, nrhs, first_psi, gather, d_err, dfirst, nsplit, dskip, nblocks};
         return dispatch_staging(g, a, s, pdl, timed, gather_only);
     }
     case QDD_PREC_F32: {
         SapArgs<float, StF32, StF32, StF32, StF32> a{
             g->geom, {c.links.as<float2>(), nullptr}, {c.sclov.as<float2>(), nullptr},
             {(float2 *)b.rho, nullptr}, (cpx<float> *)b.face, {(float2 *)b.psi, nullptr},
-            rs, ss, fs, (float)g->kappa, colour, nmr, nrhs, first_psi, gather, d_err};
+            rs, ss, fs, (float)g->kappa, colour, nmr, nrhs, first_psi, gather, d_err, dfirst, nsplit, dskip, nblocks};
         return dispatch_staging(g, a, s, pdl, timed, gather_only);
     }
     case QDD_PREC_F16S: {
         SapArgs<float, StF16, StF16, StF16, StF32> a{
             g->geom, {c.links.as<__half2>(), nullptr}, {c.sclov.as<__half2>(), c.sclov_s.as<float>()},
             {(__half2 *)b.rho, b.rho_s}, (cpx<float> *)b.face, {(float2 *)b.psi, nullptr},
-            rs, ss, fs, (float)g->kappa, colour, nmr, nrhs, first_psi, gather, d_err};
+            rs, ss, fs, (float)g->kappa, colour, nmr, nrhs, first_psi, gather, d_err, dfirst, nsplit, dskip, nblocks};
         return dispatch_staging(g, a, s, pdl, timed, gather_only);
     }
     case QDD_PREC_H16: {
@@ -910,14 +922,14 @@ qdd_status launch_sap_halfsweep(Gauge *g, qdd_prec prec, const SapBuffers &b, in
         SapArgs<float, StF16, StF16, StF32, StF32> a{
             g->geom, {h.links.as<__half2>(), nullptr}, {h.sclov.as<__half2>(), h.sclov_s.as<float>()},
             {(float2 *)b.rho, nullptr}, (cpx<float> *)b.face, {(float2 *)b.psi, nullptr},
-            rs, ss, fs, (float)g->kappa, colour, nmr, nrhs, first_psi, gather, d_err};
+            rs, ss, fs, (float)g->kappa, colour, nmr, nrhs, first_psi, gather, d_err, dfirst, nsplit, dskip, nblocks};
         return dispatch_staging(g, a, s, pdl, timed, gather_only);
     }
     case QDD_PREC_BF16S: {
         SapArgs<float, StBF16, StBF16, StBF16, StF32> a{
             g->geom, {c.links.as<__nv_bfloat162>(), nullptr}, {c.sclov.as<__nv_bfloat162>(), c.sclov_s.as<float>()},
             {(__nv_bfloat162 *)b.rho, b.rho_s}, (cpx<float> *)b.face, {(float2 *)b.psi, nullptr},
-            rs, ss, fs, (float)g->kappa, colour, nmr, nrhs, first_psi, gather, d_err};
+            rs, ss, fs, (float)g->kappa, colour, nmr, nrhs, first_psi, gather, d_err, dfirst, nsplit, dskip, nblocks};
         return dispatch_staging(g, a, s, pdl, timed, gather_only);
     }
     default: break;

@@ -29,6 +29,11 @@
 //                        extended lattice with one domain block of halo on
 //                        each side and the owned sites take theirs.
 //   FGMRES               Dot products and norms are summed over the ranks.
+// The exchanges follow the overlap order of Sec. 3.6: a half-sweep runs the
+// first and last t-block's domains first and the interior second, and their
+// face slots move on a side stream (through page-locked host memory and the
+// caller's shift hook) while the interior computes; the operator's boundary
+// planes are packed and shifted while the operator runs.
 #include <cstring>
 
 #include "internal.h"
@@ -37,7 +42,12 @@ namespace qdd {
 
 Slab::~Slab()
 {
-    if (host) cudaFreeHost(host);
+    if (side) cudaStreamSynchronize(side);
+    for (void *h : {host_face, host_op, host_red})
+        if (h) cudaFreeHost(h);
+    if (ev_in) cudaEventDestroy(ev_in);
+    if (ev_out) cudaEventDestroy(ev_out);
+    if (side) cudaStreamDestroy(side);
     if (ext) qdd_destroy_gauge(ext);
 }
 
@@ -55,14 +65,16 @@ void slab_regions(const HostGeom &hg, int colour, int out[6])
     out[5] = 6;
 }
 
-static qdd_status ensure_host(Slab &sl, size_t bytes)
+// grow a page-locked staging buffer (after the side stream's copies from it)
+static qdd_status ensure_host(Slab &sl, void *&h, size_t &have, size_t bytes)
 {
-    if (sl.host && sl.host_bytes >= bytes) return QDD_OK;
-    if (sl.host) cudaFreeHost(sl.host);
-    sl.host = nullptr;
-    sl.host_bytes = 0;
-    QDD_CUDA(cudaMallocHost(&sl.host, bytes));
-    sl.host_bytes = bytes;
+    if (h && have >= bytes) return QDD_OK;
+    QDD_CUDA(cudaStreamSynchronize(sl.side));
+    if (h) cudaFreeHost(h);
+    h = nullptr;
+    have = 0;
+    QDD_CUDA(cudaMallocHost(&h, bytes));
+    have = bytes;
     return QDD_OK;
 }
 
@@ -91,21 +103,29 @@ qdd_status slab_allreduce_dev(Gauge *g, double2 *dev, int n, cudaStream_t s)
     if (!g->slab || n <= 0) return QDD_OK;
     Slab &sl = *g->slab;
     const size_t bytes = (size_t)n * sizeof(double2);
-    QDD_TRY(ensure_host(sl, bytes));
-    QDD_CUDA(cudaMemcpyAsync(sl.host, dev, bytes, cudaMemcpyDeviceToHost, s));
+    QDD_TRY(ensure_host(sl, sl.host_red, sl.red_bytes, bytes));
+    QDD_CUDA(cudaMemcpyAsync(sl.host_red, dev, bytes, cudaMemcpyDeviceToHost, s));
     QDD_CUDA(cudaStreamSynchronize(s));
-    QDD_TRY(slab_allreduce(g, (double *)sl.host, 2 * (size_t)n));
-    QDD_CUDA(cudaMemcpyAsync(dev, sl.host, bytes, cudaMemcpyHostToDevice, s));
-    // the staging buffer is reused by the next exchange: let the copy finish
+    QDD_TRY(slab_allreduce(g, (double *)sl.host_red, 2 * (size_t)n));
+    QDD_CUDA(cudaMemcpyAsync(dev, sl.host_red, bytes, cudaMemcpyHostToDevice, s));
+    // the staging buffer is reused by the next sum: let the copy finish
     QDD_CUDA(cudaStreamSynchronize(s));
     return QDD_OK;
 }
 
-qdd_status slab_face_exchange(Gauge *g, void *face, size_t esz, int colour, int nrhs, cudaStream_t s)
+qdd_status slab_sap_halfsweep(Gauge *g, qdd_prec prec, const SapBuffers &b, int colour, int nmr, int nrhs,
+                              int first_psi, int gather, int *d_err, cudaStream_t s, bool exchange)
 {
-    if (!g->slab) return QDD_OK;
     Slab &sl = *g->slab;
     const HostGeom &hg = g->hg;
+    // boundary t-blocks first
+    QDD_TRY(launch_sap_halfsweep(g, prec, b, colour, nmr, nrhs, first_psi, gather, 0, d_err, s, false, false, 1));
+    if (exchange) QDD_CUDA(cudaEventRecord(sl.ev_in, s));
+    QDD_TRY(launch_sap_halfsweep(g, prec, b, colour, nmr, nrhs, first_psi, gather, 0, d_err, s, false, false, 2));
+    if (!exchange) return QDD_OK;
+    // meanwhile: the slots the boundary domains pushed across the slab
+    // boundaries (regions that no interior domain writes or reads)
+    const size_t esz = prec == QDD_PREC_F64 ? sizeof(double2) : sizeof(float2);
     int r[6];
     slab_regions(hg, colour, r);
     const size_t count = (size_t)hg.Vd / hg.dom[3];  // slots of a t face
@@ -114,26 +134,27 @@ qdd_status slab_face_exchange(Gauge *g, void *face, size_t esz, int colour, int 
     const size_t rb = rows * width;                  // one region of one right-hand side
     const size_t fstride = (size_t)hg.Nd * 6 * hg.nf * esz;
     const size_t tot = rb * nrhs;
-    QDD_TRY(ensure_host(sl, 4 * tot));
-    char *h = (char *)sl.host;
+    QDD_TRY(ensure_host(sl, sl.host_face, sl.face_bytes, 4 * tot));
+    char *h = (char *)sl.host_face;
     char *up = h, *dn = h + tot, *from_dn = h + 2 * tot, *from_up = h + 3 * tot;
-    char *f = (char *)face;
+    char *f = (char *)b.face;
+    QDD_CUDA(cudaStreamWaitEvent(sl.side, sl.ev_in, 0));
     for (int k = 0; k < nrhs; k++) {
         const char *ru = f + k * fstride + ((size_t)r[0] * 6 * hg.nf + hg.foff[r[2]]) * esz;
         const char *rd = f + k * fstride + ((size_t)r[3] * 6 * hg.nf + hg.foff[r[5]]) * esz;
-        QDD_CUDA(cudaMemcpy2DAsync(up + k * rb, width, ru, pitch, width, rows, cudaMemcpyDeviceToHost, s));
-        QDD_CUDA(cudaMemcpy2DAsync(dn + k * rb, width, rd, pitch, width, rows, cudaMemcpyDeviceToHost, s));
+        QDD_CUDA(cudaMemcpy2DAsync(up + k * rb, width, ru, pitch, width, rows, cudaMemcpyDeviceToHost, sl.side));
+        QDD_CUDA(cudaMemcpy2DAsync(dn + k * rb, width, rd, pitch, width, rows, cudaMemcpyDeviceToHost, sl.side));
     }
-    QDD_CUDA(cudaStreamSynchronize(s));
+    QDD_CUDA(cudaStreamSynchronize(sl.side));  // the interior may still be running
     QDD_TRY(shift(sl, up, from_dn, dn, from_up, tot));
     for (int k = 0; k < nrhs; k++) {
         char *ru = f + k * fstride + ((size_t)r[0] * 6 * hg.nf + hg.foff[r[2]]) * esz;
         char *rd = f + k * fstride + ((size_t)r[3] * 6 * hg.nf + hg.foff[r[5]]) * esz;
-        QDD_CUDA(cudaMemcpy2DAsync(ru, pitch, from_dn + k * rb, width, width, rows, cudaMemcpyHostToDevice, s));
-        QDD_CUDA(cudaMemcpy2DAsync(rd, pitch, from_up + k * rb, width, width, rows, cudaMemcpyHostToDevice, s));
+        QDD_CUDA(cudaMemcpy2DAsync(ru, pitch, from_dn + k * rb, width, width, rows, cudaMemcpyHostToDevice, sl.side));
+        QDD_CUDA(cudaMemcpy2DAsync(rd, pitch, from_up + k * rb, width, width, rows, cudaMemcpyHostToDevice, sl.side));
     }
-    // the staging buffer is reused by the next exchange: let the copies finish
-    QDD_CUDA(cudaStreamSynchronize(s));
+    QDD_CUDA(cudaEventRecord(sl.ev_out, sl.side));
+    QDD_CUDA(cudaStreamWaitEvent(s, sl.ev_out, 0));
     return QDD_OK;
 }
 
@@ -227,42 +248,62 @@ __global__ void __launch_bounds__(128) k_slab_fix(double2 *out, PlaneAddr pa, in
     }
 }
 
-qdd_status slab_dslash_fix(Gauge *g, const void *in, bool in_f32, double2 *out, bool residual, bool host_layout,
-                           int nrhs, cudaStream_t s)
+qdd_status slab_dslash_begin(Gauge *g, const void *in, bool in_f32, bool host_layout, int nrhs, cudaStream_t s)
 {
     if (!g->slab) return QDD_OK;
     Slab &sl = *g->slab;
     const HostGeom &hg = g->hg;
     const size_t per = (size_t)nrhs * sl.Ls * 6;  // double2 of one buffer
     if (sl.buf_rhs < (size_t)nrhs) {
+        QDD_CUDA(cudaStreamSynchronize(sl.side));
         QDD_TRY(sl.bufs.alloc(g->ctx, 4 * per * sizeof(double2)));
         sl.buf_rhs = nrhs;
     }
-    double2 *own_b = sl.bufs.as<double2>(), *own_f = own_b + per, *got_b = own_b + 2 * per, *got_f = own_b + 3 * per;
+    const size_t bytes = per * sizeof(double2);
+    QDD_TRY(ensure_host(sl, sl.host_op, sl.op_bytes, 4 * bytes));
+    double2 *own_b = sl.bufs.as<double2>(), *own_f = own_b + per;
+    sl.op_host_layout = host_layout;
     PlaneAddr pa{host_layout ? nullptr : sl.plane_base.as<int64_t>(), host_layout ? 1 : (int64_t)hg.Vd, sl.Ls, sl.lt};
     const int64_t fstride = (int64_t)hg.V * 12;
     dim3 grid((sl.Ls + 127) / 128, nrhs);
+    // the input is complete in stream s's order
+    QDD_CUDA(cudaEventRecord(sl.ev_in, s));
+    QDD_CUDA(cudaStreamWaitEvent(sl.side, sl.ev_in, 0));
     g->ctx->timer.count(K_OTHER);
     if (in_f32)
-        k_slab_pack<float2><<<grid, 128, 0, s>>>((const float2 *)in, pa, fstride, g->links64.as<double2>(),
-                                                 sl.last_link.as<int64_t>(), hg.Vd, nrhs, own_b, own_f);
+        k_slab_pack<float2><<<grid, 128, 0, sl.side>>>((const float2 *)in, pa, fstride, g->links64.as<double2>(),
+                                                       sl.last_link.as<int64_t>(), hg.Vd, nrhs, own_b, own_f);
     else
-        k_slab_pack<double2><<<grid, 128, 0, s>>>((const double2 *)in, pa, fstride, g->links64.as<double2>(),
-                                                  sl.last_link.as<int64_t>(), hg.Vd, nrhs, own_b, own_f);
+        k_slab_pack<double2><<<grid, 128, 0, sl.side>>>((const double2 *)in, pa, fstride, g->links64.as<double2>(),
+                                                        sl.last_link.as<int64_t>(), hg.Vd, nrhs, own_b, own_f);
     QDD_CUDA(cudaGetLastError());
+    // own_b, own_f adjacent: one copy
+    QDD_CUDA(cudaMemcpyAsync(sl.host_op, own_b, 2 * bytes, cudaMemcpyDeviceToHost, sl.side));
+    return QDD_OK;
+}
+
+qdd_status slab_dslash_end(Gauge *g, double2 *out, bool residual, int nrhs, cudaStream_t s)
+{
+    if (!g->slab) return QDD_OK;
+    Slab &sl = *g->slab;
+    const HostGeom &hg = g->hg;
+    const size_t per = (size_t)nrhs * sl.Ls * 6;
     const size_t bytes = per * sizeof(double2);
-    QDD_TRY(ensure_host(sl, 4 * bytes));
-    char *h = (char *)sl.host;
-    QDD_CUDA(cudaMemcpyAsync(h, own_b, 2 * bytes, cudaMemcpyDeviceToHost, s));  // own_b, own_f adjacent
-    QDD_CUDA(cudaStreamSynchronize(s));
+    double2 *own_b = sl.bufs.as<double2>(), *own_f = own_b + per, *got_b = own_b + 2 * per, *got_f = own_b + 3 * per;
+    char *h = (char *)sl.host_op;
+    QDD_CUDA(cudaStreamSynchronize(sl.side));  // packed planes on the host; the operator may still run
     QDD_TRY(shift(sl, h, h + 2 * bytes, h + bytes, h + 3 * bytes, bytes));
-    QDD_CUDA(cudaMemcpyAsync(got_b, h + 2 * bytes, 2 * bytes, cudaMemcpyHostToDevice, s));
+    QDD_CUDA(cudaMemcpyAsync(got_b, h + 2 * bytes, 2 * bytes, cudaMemcpyHostToDevice, sl.side));
+    QDD_CUDA(cudaEventRecord(sl.ev_out, sl.side));
+    QDD_CUDA(cudaStreamWaitEvent(s, sl.ev_out, 0));
+    PlaneAddr pa{sl.op_host_layout ? nullptr : sl.plane_base.as<int64_t>(), sl.op_host_layout ? 1 : (int64_t)hg.Vd,
+                 sl.Ls, sl.lt};
     g->ctx->timer.count(K_OTHER);
     dim3 grid2((sl.Ls + 127) / 128, 2 * nrhs);
-    k_slab_fix<<<grid2, 128, 0, s>>>(out, pa, fstride, g->links64.as<double2>(), sl.last_link.as<int64_t>(), hg.Vd,
-                                     nrhs, residual ? g->kappa : -g->kappa, own_b, own_f, got_b, got_f);
+    k_slab_fix<<<grid2, 128, 0, s>>>(out, pa, (int64_t)hg.V * 12, g->links64.as<double2>(),
+                                     sl.last_link.as<int64_t>(), hg.Vd, nrhs, residual ? g->kappa : -g->kappa, own_b,
+                                     own_f, got_b, got_f);
     QDD_CUDA(cudaGetLastError());
-    QDD_CUDA(cudaStreamSynchronize(s));
     return QDD_OK;
 }
 
@@ -324,6 +365,9 @@ qdd_status slab_setup(Gauge *g, qdd_gauge *ext, const qdd_comm &comm)
     QDD_CUDA(cudaMemcpy(sl->ext_map.p, map.data(), map.size() * sizeof(int), cudaMemcpyHostToDevice));
     QDD_CUDA(cudaMemcpy(sl->plane_base.p, base.data(), base.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
     QDD_CUDA(cudaMemcpy(sl->last_link.p, link.data(), link.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+    QDD_CUDA(cudaStreamCreateWithFlags(&sl->side, cudaStreamNonBlocking));
+    QDD_CUDA(cudaEventCreateWithFlags(&sl->ev_in, cudaEventDisableTiming));
+    QDD_CUDA(cudaEventCreateWithFlags(&sl->ev_out, cudaEventDisableTiming));
     g->slab = std::move(sl);
     return QDD_OK;
 }

@@ -235,9 +235,10 @@ qdd_status solve_impl(Gauge *g, Workspace *wsp, const double *b_in, double *x_ou
         if (cycle == 0)
             QDD_CUDA(cudaMemcpyAsync(V, Bv, (size_t)n * 16 * B, cudaMemcpyDeviceToDevice, s));
         else {
+            QDD_TRY(slab_dslash_begin(g, X, false, false, B, s));  // sharded: boundary planes
             QDD_TRY(launch_dslash(g, QDD_PREC_F64, QDD_PREC_F64, X, nullptr, QDD_PREC_F64, pending_dr ? w.Vt.as<double2>() : V,
                                   nullptr, QDD_PREC_F64, Bv, B, s));
-            QDD_TRY(slab_dslash_fix(g, X, false, V, true, false, B, s));
+            QDD_TRY(slab_dslash_end(g, V, true, B, s));
         }
         double2 *R0 = (cycle > 0 && pending_dr) ? w.Vt.as<double2>() : V;
         for (int r = 0; r < B; r++) QDD_TRY(blas_norm2(ctx, R0 + r * n, n, dev + sm.nrm1() + r, scr, s));
@@ -402,13 +403,15 @@ qdd_status solve_impl(Gauge *g, Workspace *wsp, const double *b_in, double *x_ou
                 rho_ready = false;
                 sb.psi = zj;
                 SeqScope seq(ctx->timer, K_SAP, s);
-                const size_t fesz = sp == QDD_PREC_F64 ? sizeof(double2) : sizeof(float2);
                 for (int hs = 0; hs < 2 * p->ncy; hs++) {
                     // sharded: the face slots crossing the slab boundaries move
-                    // between half-sweeps (no dependent launch across them)
-                    QDD_TRY(launch_sap_halfsweep(g, sp, sb, hs & 1, p->nmr, B, hs < 2, hs >= 1, 0, w.err.as<int>(), s,
-                                                 hs >= 1 && !sharded, false));
-                    if (sharded && hs + 1 < 2 * p->ncy) QDD_TRY(slab_face_exchange(g, w.face.p, fesz, hs & 1, B, s));
+                    // while the interior domains are swept
+                    if (sharded)
+                        QDD_TRY(slab_sap_halfsweep(g, sp, sb, hs & 1, p->nmr, B, hs < 2, hs >= 1, w.err.as<int>(), s,
+                                                   hs + 1 < 2 * p->ncy));
+                    else
+                        QDD_TRY(launch_sap_halfsweep(g, sp, sb, hs & 1, p->nmr, B, hs < 2, hs >= 1, 0,
+                                                     w.err.as<int>(), s, hs >= 1, false));
                 }
             } else {
                 QDD_TRY(launch_spinor_convert(g, vj, nullptr, QDD_PREC_F64, zj, nullptr, zp, B, s));
@@ -420,6 +423,7 @@ qdd_status solve_impl(Gauge *g, Workspace *wsp, const double *b_in, double *x_ou
             for (int r = 0; r < B; r++)
                 if (open[r]) est_now = std::max(est_now, j == j0 ? rel[r] : est[r]);
             const bool relaxed = p->relax_eta > 0 && p->relax_eta * est_now <= 0.1 * p->tol;
+            QDD_TRY(slab_dslash_begin(g, zj, zp == QDD_PREC_F32, false, B, s));  // sharded: boundary planes
             if (relaxed)
                 QDD_TRY(launch_dslash(g, QDD_PREC_F32, QDD_PREC_F32, zj, nullptr, QDD_PREC_F32, wv, nullptr,
                                       QDD_PREC_F64, nullptr, B, s));
@@ -429,13 +433,15 @@ qdd_status solve_impl(Gauge *g, Workspace *wsp, const double *b_in, double *x_ou
             else
                 QDD_TRY(launch_dslash(g, QDD_PREC_F32, QDD_PREC_F32, zj, nullptr, QDD_PREC_F32, wv, nullptr,
                                       QDD_PREC_F64, nullptr, B, s));
-            QDD_TRY(slab_dslash_fix(g, zj, zp == QDD_PREC_F32, wv, false, false, B, s));
+            QDD_TRY(slab_dslash_end(g, wv, false, B, s));
             // classical Gram-Schmidt, pass 1 (dots include <w, w>)
             for (int r = 0; r < B; r++) {
                 if (!open[r]) continue;
+                // <w, w> (the last dot) only feeds the selective re-orthogonalisation test
                 double2 *d1 = dev + sm.dots1() + (size_t)r * (m + 2);
-                QDD_TRY(blas_cdot_multi(ctx, V + r * n, j + 2, ldV, wv + r * n, n, d1, scr, s));
-                QDD_TRY(slab_allreduce_dev(g, d1, j + 2, s));  // sharded: sums over the ranks
+                const int nd = p->reorth == 1 ? j + 2 : j + 1;
+                QDD_TRY(blas_cdot_multi(ctx, V + r * n, nd, ldV, wv + r * n, n, d1, scr, s));
+                QDD_TRY(slab_allreduce_dev(g, d1, nd, s));  // sharded: sums over the ranks
                 QDD_TRY(blas_caxpy_multi_norm(ctx, V + r * n, j + 1, ldV, d1, wv + r * n, n, dev + sm.nrm1() + r,
                                               scr, s));
                 QDD_TRY(slab_allreduce_dev(g, dev + sm.nrm1() + r, 1, s));
