@@ -79,6 +79,32 @@ __device__ __forceinline__ void load_link(const Field<S> &U, int d, int s, int m
     }
 }
 
+// one hop of a neighbour spinor x stored with per-site scale sc: the hop is
+// linear, so the scale multiplies its 6-component result, not the 12 inputs
+template <int MU, int SGN, bool SCALED, typename R>
+__device__ __forceinline__ void hop_scaled(const cpx<R> *U, const cpx<R> *x, R sc, cpx<R> *acc)
+{
+    cpx<R> h[6], w[6];
+    project<MU, SGN>(x, h);
+    su3_mul_half<(SGN < 0)>(U, h, w);
+    if (SCALED) {
+#pragma unroll
+        for (int k = 0; k < 6; k++) w[k] = sc * w[k];
+    }
+    reconstruct_add<MU, SGN>(w, acc);
+}
+
+// the unscaled components of a spinor and, for a 16-bit field, its scale
+template <typename R, typename S>
+__device__ __forceinline__ R load_spinor_raw(const Field<S> &f, int64_t gi_plane_base, int64_t sidx, int Vd,
+                                             cpx<R> *x)
+{
+    const typename S::T2 *p = f.p + gi_plane_base;
+#pragma unroll
+    for (int k = 0; k < 12; k++) x[k] = ld_c<R>(p + (int64_t)k * Vd);
+    return S::kScaled ? (R)__ldg(f.scale + sidx) : (R)1;
+}
+
 template <int MU, typename R, typename SL, typename SI, bool L12>
 __device__ __forceinline__ void dslash_dir(const Geom &g, const Field<SL> &U, const Field<SI> &in, int64_t rbase,
                                            int64_t sbase, int d, int s, cpx<R> *acc)
@@ -89,9 +115,10 @@ __device__ __forceinline__ void dslash_dir(const Geom &g, const Field<SL> &U, co
         int nd = (e & kCross) ? __ldg(g.nbd + d * 8 + 2 * MU) : d;
         int ns = e & kSlotMask;
         if (QDD_IN_RANGE(nd, 0, g.Nd) && QDD_IN_RANGE(ns, 0, g.Vd)) {
-            load_spinor<R, SI>(in, rbase + (int64_t)nd * 12 * g.Vd + ns, sbase + (int64_t)nd * g.Vd + ns, g.Vd, x);
+            R sc = load_spinor_raw<R, SI>(in, rbase + (int64_t)nd * 12 * g.Vd + ns, sbase + (int64_t)nd * g.Vd + ns,
+                                          g.Vd, x);
             load_link<R, SL, L12>(U, d, s, MU, g.Vd, u);
-            hop<MU, +1>(u, x, acc);
+            hop_scaled<MU, +1, SI::kScaled>(u, x, sc, acc);
         }
     }
     {
@@ -99,9 +126,10 @@ __device__ __forceinline__ void dslash_dir(const Geom &g, const Field<SL> &U, co
         int nd = (e & kCross) ? __ldg(g.nbd + d * 8 + 2 * MU + 1) : d;
         int ns = e & kSlotMask;
         if (QDD_IN_RANGE(nd, 0, g.Nd) && QDD_IN_RANGE(ns, 0, g.Vd)) {
-            load_spinor<R, SI>(in, rbase + (int64_t)nd * 12 * g.Vd + ns, sbase + (int64_t)nd * g.Vd + ns, g.Vd, x);
+            R sc = load_spinor_raw<R, SI>(in, rbase + (int64_t)nd * 12 * g.Vd + ns, sbase + (int64_t)nd * g.Vd + ns,
+                                          g.Vd, x);
             load_link<R, SL, L12>(U, nd, ns, MU, g.Vd, u);
-            hop<MU, -1>(u, x, acc);
+            hop_scaled<MU, -1, SI::kScaled>(u, x, sc, acc);
         }
     }
 }
@@ -142,11 +170,11 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 1) k_dslash(Geom g, 
 #pragma unroll
                 for (int k = 0; k < 18; k++) m[k] = ld_c<R>(p + (int64_t)(blk * 18 + k) * g.Vd);
             }
-            if (SC::kScaled) {
-#pragma unroll
-                for (int k = 0; k < 18; k++) m[k] = sc * m[k];
-            }
             herm6_mul(m, x + 6 * blk, y + 6 * blk);
+        }
+        if (SC::kScaled) {  // the clover's per-site scale on the 12 products
+#pragma unroll
+            for (int k = 0; k < 12; k++) y[k] = sc * y[k];
         }
     }
 #pragma unroll
