@@ -86,6 +86,8 @@ def parse():
                     help="workload configuration (4, the largest single-GPU one, is the default line)")
     ap.add_argument("--serve", action="store_true", help="run the serving mix instead of single solves")
     ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-in-line", type=int, default=100,
+                    help="requests of the serving mix reported in the solve line (0 = none)")
     ap.add_argument("--op-bench", action="store_true", help="time only the full-lattice operator")
     ap.add_argument("--mg", action="store_true",
                     help="time-to-solution near the critical kappa: Schwarz-only against the two-level multigrid")
@@ -651,6 +653,20 @@ def run_qdd(args):
         except Exception as e:  # the GPU number stands without it
             cpu = {"value": None, "unit": "ms", "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
 
+    # a shorter serving mix (its own context; the workload's fields are freed first)
+    serving = None
+    if rank == 0 and world == 1 and args.serve_in_line > 0:
+        qdd.qdd_destroy_gauge(g)
+        qdd.qdd_destroy(ctx)
+        g = ctx = None
+        try:
+            sv = serve_mix(args.serve_in_line)
+            serving = {k: sv[k] for k in ("p50_ms", "p99_ms", "solves_per_s", "requests", "converged",
+                                          "offered_rate_per_s", "gpu_busy_fraction", "wall_s")}
+            serving["workload"] = sv["config"]["workload"]
+        except Exception as e:  # the solve line stands without it
+            serving = {"failed": repr(e)}
+
     if rank == 0:
         last = reps[-1]
         line = {"metric": METRIC, "value": ms_step, "unit": "ms", "n_gpus": world, "steps": args.steps,
@@ -671,12 +687,13 @@ def run_qdd(args):
                 "converged": bool(last["converged"]),
                 "roofline": roof, "roofline_fp64_vector_algebra": blas_roof, "fma_peaks": fma,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-                "dslash": dslash, "plain_fp64": plain, "unbatched": unbatched}
+                "dslash": dslash, "plain_fp64": plain, "unbatched": unbatched, "serving": serving}
         if parity is not None:
             line["parity"] = parity
         print(json.dumps(line), flush=True)
-    qdd.qdd_destroy_gauge(g)
-    qdd.qdd_destroy(ctx)
+    if g is not None:
+        qdd.qdd_destroy_gauge(g)
+        qdd.qdd_destroy(ctx)
     if dist is not None:
         dist.destroy_process_group()
 
@@ -816,12 +833,15 @@ def run_serve(args):
     [0.120, 0.135] (four resident values) and 1-12 right-hand sides, FP32
     preconditioner, double-float Arnoldi operator, tol 1e-10, admission by an
     80% HBM budget; reports p50/p99 latency (submit to result) and solves/s."""
-    import torch
-
-    from paper_1502_04025_gb300 import build, inputs
+    from paper_1502_04025_gb300 import build
 
     build.build()
-    from paper_1502_04025_gb300 import qdd
+    print(json.dumps(serve_mix(args.serve_requests)), flush=True)
+
+
+def serve_mix(n_requests):
+    """The serving mix of run_serve with n_requests requests; returns its JSON record."""
+    from paper_1502_04025_gb300 import inputs, qdd
 
     ctx = qdd.qdd_create(0, 0)
     qdd.qdd_serve_config(ctx, 4)
@@ -834,7 +854,7 @@ def run_serve(args):
             gauges[(li, ki)] = g
         del U
     rng = np.random.Generator(np.random.Philox(3001))
-    n = args.serve_requests
+    n = n_requests
     reqs = []
     for i in range(n):
         li = int(rng.integers(0, len(SERVE_LATTICES)))
@@ -920,10 +940,10 @@ def run_serve(args):
                                    "kappa in {0.120,0.125,0.130,0.135}, 1-12 rhs, FP32 SAP, tol 1e-10",
                        "slots": 4, "hbm_budget_bytes": budget, "resident_gauge_bytes": used},
             "calibration_s": {f"{SERVE_LATTICES[li][0]}x{r}": v for (li, r), v in cal.items()}}
-    print(json.dumps(line), flush=True)
     for g in gauges.values():
         qdd.qdd_destroy_gauge(g)
     qdd.qdd_destroy(ctx)
+    return line
 
 
 def main():

@@ -59,16 +59,20 @@ def test_deflated_restart_keeps_the_arnoldi_relation(ora, prob):
         k = Z.shape[0]
         DZ = np.stack([P.D(Z[i]) for i in range(k)])
         seen.append((np.linalg.norm(DZ - (H.T @ V)) / np.linalg.norm(DZ),
-                     np.abs(V.conj() @ V.T - np.eye(k + 1)).max()))
+                     np.abs(V.conj() @ V.T - np.eye(k + 1)).max(), np.linalg.norm(c)))
 
     x, info = dr.fgmres_dr(P, b, 1e-12, m=6, k=3, max_cycles=40, state_hook=hook)
-    assert info["converged"] and seen
-    # the relation holds at every deflated restart; orthogonality is checked
-    # at the first one (near convergence the Gram-Schmidt steps project out
-    # almost all of w and the basis loses orthogonality, as any GMRES does)
-    for rel_rel, _ in seen:
+    assert info["converged"] and len(seen) >= 8
+    # The relation holds at every deflated restart.  So does orthonormality,
+    # to the accuracy the restart can give it: the least-squares residual
+    # rho, recycled as the last basis vector, carries an absolute error of
+    # order eps |b|, so after normalisation the basis is orthonormal to about
+    # eps |b| / |rho| (|rho| = |c|), which grows as the solve converges.  A
+    # recombination that mixes the wrong columns breaks it by O(1).
+    eps, bn = np.finfo(float).eps, np.linalg.norm(b)
+    for rel_rel, orth, cn in seen:
         assert rel_rel <= 1e-11
-    assert seen[0][1] <= 1e-12
+        assert orth <= 16 * eps * bn / cn, (orth, cn)
 
 
 def test_deflation_reaches_lu_and_cuts_iterations(ora, prob):
