@@ -101,6 +101,8 @@ def parse():
     ap.add_argument("--no-dslash", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true", help="skip the plain FP64 path on the same system")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--dist-backend", choices=["nccl", "gloo"], default="nccl",
+                    help="torch.distributed backend of a multi-GPU run (gloo: exchanges through host tensors)")
     ap.add_argument("--replicas", action="store_true",
                     help="with several GPUs, solve one copy of the workload per GPU instead of sharding it")
     return ap.parse_args()
@@ -399,13 +401,18 @@ def run_qdd(args):
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    # one GPU per rank; with fewer GPUs than ranks (a check of the sharded path
+    # with --dist-backend gloo) ranks share them
+    local = int(os.environ.get("LOCAL_RANK", "0")) % max(1, torch.cuda.device_count())
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
         import torch.distributed as dist
 
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if args.dist_backend == "nccl":
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group("gloo")
 
     def barrier():
         if dist is not None:
@@ -436,7 +443,7 @@ def run_qdd(args):
             shard_reason = str(e)
     if shard is not None:
         t0, lt = shard
-        comm = qdist.TorchComm(device=torch.device("cuda", local))
+        comm = qdist.TorchComm(device=torch.device("cuda", local) if args.dist_backend == "nccl" else None)
         g = qdd.qdd_create_gauge_field_slab(ctx, qdist.local_lattice(W["L"], lt), W["dom"],
                                             qdist.extended_links(U, W["L"], W["dom"], t0, lt), comm)
         b = qdist.local_field(b, W["L"], t0, lt)
@@ -486,7 +493,7 @@ def run_qdd(args):
     ms_total = e0.elapsed_time(e1)
     kt = qdd.qdd_get_kernel_times(ctx, reset=True)
     qdd.qdd_set_profiling(ctx, 0)
-    ms_step = max_over_ranks(ms_total / args.steps, dist, "cuda")
+    ms_step = max_over_ranks(ms_total / args.steps, dist, "cuda" if args.dist_backend == "nccl" else "cpu")
     launches = int(sum(r["kernel_launches"] for r in reps))
 
     # ---- kernel-class shares from one extra solve with every class event-timed

@@ -208,11 +208,13 @@ qdd_status qdd_link_compression(qdd_gauge *g, int *two_rows, int *is_su3);
 /*
  * Form of the Schwarz block kernel (the result is the same bits either way):
  * 0 (default) stages the domain's links and, when it fits, its clover in
- * shared memory; 1 stages the links only, reads the clover through the
+ * shared memory, with the domain size fixed at compile time for 4^4 domains
+ * in 16-bit storage; 1 stages the links only, reads the clover through the
  * cache and is compiled for three CTAs per SM (FP32 arithmetic on domains of
- * at most 256 sites; otherwise form 0 runs).  The paper sizes its domains to
- * the cache (Sec. 3.3); on the GPU the choice trades staged data against the
- * number of domains an SM holds.
+ * at most 256 sites; otherwise form 0 runs); 2 is form 0 with the domain size
+ * always taken at run time.  The paper sizes its domains to the cache
+ * (Sec. 3.3); on the GPU the choice trades staged data against the number of
+ * domains an SM holds.
  */
 qdd_status qdd_set_schwarz_variant(qdd_gauge *g, int variant);
 

@@ -383,13 +383,16 @@ enum SapPhase : int {
 // MAXT / MINB: the launch bounds.  The default form allows 256 threads (an
 // 8x4^3 domain); the occupancy form (128 threads, 3 CTAs per SM) caps the
 // registers at 170 so that three 4^4 domains run on an SM at once.
+// VH: the half-domain size when fixed at compile time (0: taken from the
+// geometry); a fixed size turns the shared-memory offsets of the stencil
+// into immediates.
 template <typename R, typename SL, typename SC, typename SS, typename SP, bool STL, bool STC, int MAXT = 256,
-          int MINB = 1>
+          int MINB = 1, int VH = 0>
 __global__ void __launch_bounds__(MAXT, MINB) k_sap(const SapArgs<R, SL, SC, SS, SP> a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     const Geom &g = a.g;
-    const int Vd = g.Vd, Vh = g.Vh;
+    const int Vd = VH ? 2 * VH : g.Vd, Vh = VH ? VH : g.Vh;
     const int i = threadIdx.x;
     const int bx = blockIdx.x;
     const int d = a.colour * g.Nd2 + a.dfirst + (bx < a.nsplit ? bx : bx + a.dskip);
@@ -752,12 +755,12 @@ __global__ void __launch_bounds__(128) k_sap_face_apply(const Geom g, const Fiel
 // ---------------------------------------------------------------- launch
 
 template <typename R, typename SL, typename SC, typename SS, typename SP, bool STL, bool STC, int MAXT = 256,
-          int MINB = 1>
+          int MINB = 1, int VH = 0>
 static qdd_status run_sap(Gauge *g, const SapArgs<R, SL, SC, SS, SP> &a, cudaStream_t s, bool pdl, bool timed)
 {
     const HostGeom &hg = g->hg;
     size_t smem = sap_smem_layout<R, SL, SC>(hg.Vd, STL, STC);
-    auto kern = k_sap<R, SL, SC, SS, SP, STL, STC, MAXT, MINB>;
+    auto kern = k_sap<R, SL, SC, SS, SP, STL, STC, MAXT, MINB, VH>;
     static thread_local size_t configured = 0;
     if (configured < smem) {
         QDD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -828,8 +831,13 @@ static qdd_status dispatch_staging(Gauge *g, const SapArgs<R, SL, SC, SS, SP> &a
             3 * (sap_smem_layout<R, SL, SC>(Vd, true, false) + 1024) <= smem_per_sm())
             return run_sap<R, SL, SC, SS, SP, true, false, 128, 3>(g, a, s, pdl, timed);
     }
-    if (sap_smem_layout<R, SL, SC>(Vd, true, true) <= lim)
+    if (sap_smem_layout<R, SL, SC>(Vd, true, true) <= lim) {
+        // 4^4 domains (the 16-bit workloads' shape): the size fixed at compile time
+        if constexpr (sizeof(R) == 4 && !std::is_same<SL, StF32>::value)
+            if (hg.Vh == 128 && g->sap_variant == 0)
+                return run_sap<R, SL, SC, SS, SP, true, true, 128, 2, 128>(g, a, s, pdl, timed);
         return run_sap<R, SL, SC, SS, SP, true, true>(g, a, s, pdl, timed);
+    }
     if (sap_smem_layout<R, SL, SC>(Vd, true, false) <= lim)
         return run_sap<R, SL, SC, SS, SP, true, false>(g, a, s, pdl, timed);
     if (sap_smem_layout<R, SL, SC>(Vd, false, false) <= lim)
