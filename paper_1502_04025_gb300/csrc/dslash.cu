@@ -134,10 +134,26 @@ __device__ __forceinline__ void dslash_dir(const Geom &g, const Field<SL> &U, co
     }
 }
 
-template <typename R, typename SL, typename SC, typename SI, typename SO, bool RESID, bool L12>
-__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 1) k_dslash(Geom g, Field<SL> U, Field<SC> A, Field<SI> in, Field<SO> out,
+// The geometry with the domain volume fixed at compile time when VD > 0 (a
+// power of two): plane strides and site splits become immediates.
+template <int VD>
+__device__ __forceinline__ Geom fixed_geom(const Geom &g0)
+{
+    Geom g = g0;
+    if (VD > 0) {
+        static_assert(VD <= 0 || (VD & (VD - 1)) == 0, "a fixed domain volume is a power of two");
+        g.Vd = VD;
+        g.Vh = VD / 2;
+        g.vd_shift = VD == 256 ? 8 : (VD == 512 ? 9 : (VD == 128 ? 7 : g0.vd_shift));
+    }
+    return g;
+}
+
+template <typename R, typename SL, typename SC, typename SI, typename SO, bool RESID, bool L12, int VD = 0>
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 1) k_dslash(Geom g0, Field<SL> U, Field<SC> A, Field<SI> in, Field<SO> out,
                                                 const double2 *b, R kappa)
 {
+    const Geom g = fixed_geom<VD>(g0);
     int gi = blockIdx.x * blockDim.x + threadIdx.x;
     if (gi >= g.V) return;
     const int64_t r = blockIdx.y;
@@ -305,10 +321,11 @@ __device__ __forceinline__ void hop_df_rt(const HopSpin &hs, const cdf *U, const
     }
 }
 
-template <typename SI>
-__global__ void __launch_bounds__(128, 4) k_dslash_df(Geom g, const float4 *U, const float4 *A,
+template <typename SI, int VD = 0>
+__global__ void __launch_bounds__(128, 4) k_dslash_df(Geom g0, const float4 *U, const float4 *A,
                                                    const typename SI::T2 *in, double2 *out, df kappa)
 {
+    const Geom g = fixed_geom<VD>(g0);
     int gi = blockIdx.x * blockDim.x + threadIdx.x;
     if (gi >= g.V) return;
     const int64_t rbase = (int64_t)blockIdx.y * g.V * 12;
@@ -403,7 +420,10 @@ static qdd_status run_dslash(Gauge *g, Field<SL> U, Field<SC> A, const void *in,
     Field<SO> fo{(typename SO::T2 *)out, out_s};
     dim3 grid((g->hg.V + 127) / 128, nrhs);
     LaunchScope ls(g->ctx->timer, K_DSLASH, s);
-    k_dslash<R, SL, SC, SI, SO, RESID, L12><<<grid, 128, 0, s>>>(g->geom, U, A, fi, fo, b, (R)g->kappa);
+    if (g->hg.Vd == 256)  // 4^4 domains: the volume fixed at compile time
+        k_dslash<R, SL, SC, SI, SO, RESID, L12, 256><<<grid, 128, 0, s>>>(g->geom, U, A, fi, fo, b, (R)g->kappa);
+    else
+        k_dslash<R, SL, SC, SI, SO, RESID, L12><<<grid, 128, 0, s>>>(g->geom, U, A, fi, fo, b, (R)g->kappa);
     QDD_CUDA(cudaGetLastError());
     return QDD_OK;
 }
@@ -451,9 +471,16 @@ qdd_status launch_dslash(Gauge *g, qdd_prec arith, qdd_prec fp, const void *in, 
         dim3 grid((g->hg.V + 127) / 128, nrhs);
         df kap = {(float)g->kappa, (float)(g->kappa - (double)(float)g->kappa)};
         LaunchScope ls(g->ctx->timer, K_DSLASH, s);
-        if (ip == QDD_PREC_F32)
+        const bool v256 = g->hg.Vd == 256;  // 4^4 domains: the volume fixed at compile time
+        if (ip == QDD_PREC_F32 && v256)
+            k_dslash_df<StF32, 256><<<grid, 128, 0, s>>>(g->geom, c.links.as<float4>(), c.clov.as<float4>(),
+                                                         (const float2 *)in, (double2 *)out, kap);
+        else if (ip == QDD_PREC_F32)
             k_dslash_df<StF32><<<grid, 128, 0, s>>>(g->geom, c.links.as<float4>(), c.clov.as<float4>(),
                                                     (const float2 *)in, (double2 *)out, kap);
+        else if (ip == QDD_PREC_F64 && v256)
+            k_dslash_df<StF64, 256><<<grid, 128, 0, s>>>(g->geom, c.links.as<float4>(), c.clov.as<float4>(),
+                                                         (const double2 *)in, (double2 *)out, kap);
         else if (ip == QDD_PREC_F64)
             k_dslash_df<StF64><<<grid, 128, 0, s>>>(g->geom, c.links.as<float4>(), c.clov.as<float4>(),
                                                     (const double2 *)in, (double2 *)out, kap);

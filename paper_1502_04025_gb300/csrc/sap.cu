@@ -838,8 +838,13 @@ static qdd_status dispatch_staging(Gauge *g, const SapArgs<R, SL, SC, SS, SP> &a
                 return run_sap<R, SL, SC, SS, SP, true, true, 128, 2, 128>(g, a, s, pdl, timed);
         return run_sap<R, SL, SC, SS, SP, true, true>(g, a, s, pdl, timed);
     }
-    if (sap_smem_layout<R, SL, SC>(Vd, true, false) <= lim)
+    if (sap_smem_layout<R, SL, SC>(Vd, true, false) <= lim) {
+        // 8x4^3 domains with FP32 links (the clover does not fit): the size fixed at compile time
+        if constexpr (sizeof(R) == 4 && std::is_same<SL, StF32>::value)
+            if (hg.Vh == 256 && g->sap_variant == 0)
+                return run_sap<R, SL, SC, SS, SP, true, false, 256, 1, 256>(g, a, s, pdl, timed);
         return run_sap<R, SL, SC, SS, SP, true, false>(g, a, s, pdl, timed);
+    }
     if (sap_smem_layout<R, SL, SC>(Vd, false, false) <= lim)
         return run_sap<R, SL, SC, SS, SP, false, false>(g, a, s, pdl, timed);
     set_error("domain of %d sites does not fit in shared memory", Vd);
