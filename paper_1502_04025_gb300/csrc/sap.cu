@@ -166,6 +166,7 @@ __host__ __device__ constexpr size_t sap_smem_layout(int Vd, bool stl, bool stc)
 template <typename R, typename SL, typename SC, typename SS, typename SP, bool STL, bool STC>
 struct SapBlock {
     const SapArgs<R, SL, SC, SS, SP> &a;
+    const Geom &g;  // the kernel's geometry (with compile-time fields for a fixed domain shape)
     int d, Vd, Vh;
     const typename SL::T2 *sL;
     const typename SC::T2 *sC;
@@ -244,22 +245,22 @@ struct SapBlock {
     __device__ __forceinline__ void face_out_dir(int s, const uint16_t *nb, uint32_t fc, const int *nbd,
                                                  const cpx<R> *dl, cpx<R> *fb) const
     {
-        const int nf = a.g.nf, t = (fc >> (8 * MU)) & 255;
+        const int nf = g.nf, t = (fc >> (8 * MU)) & 255;
         cpx<R> h[6];
-        if ((nb[2 * MU] & kCross) && QDD_IN_RANGE(nbd[2 * MU], 0, a.g.Nd) &&
-            QDD_IN_RANGE(a.g.foff[2 * MU + 1] + t, 0, nf)) {
+        if ((nb[2 * MU] & kCross) && QDD_IN_RANGE(nbd[2 * MU], 0, g.Nd) &&
+            QDD_IN_RANGE(g.foff[2 * MU + 1] + t, 0, nf)) {
             cpx<R> u[9], w[6];
             project<MU, -1>(dl, h);
             link(d, s, MU, u);
             su3_mul_half<true>(u, h, w);
-            cpx<R> *dst = fb + (int64_t)nbd[2 * MU] * 6 * nf + a.g.foff[2 * MU + 1] + t;
+            cpx<R> *dst = fb + (int64_t)nbd[2 * MU] * 6 * nf + g.foff[2 * MU + 1] + t;
 #pragma unroll
             for (int k = 0; k < 6; k++) dst[k * nf] = w[k];
         }
-        if ((nb[2 * MU + 1] & kCross) && QDD_IN_RANGE(nbd[2 * MU + 1], 0, a.g.Nd) &&
-            QDD_IN_RANGE(a.g.foff[2 * MU] + t, 0, nf)) {
+        if ((nb[2 * MU + 1] & kCross) && QDD_IN_RANGE(nbd[2 * MU + 1], 0, g.Nd) &&
+            QDD_IN_RANGE(g.foff[2 * MU] + t, 0, nf)) {
             project<MU, +1>(dl, h);
-            cpx<R> *dst = fb + (int64_t)nbd[2 * MU + 1] * 6 * nf + a.g.foff[2 * MU] + t;
+            cpx<R> *dst = fb + (int64_t)nbd[2 * MU + 1] * 6 * nf + g.foff[2 * MU] + t;
 #pragma unroll
             for (int k = 0; k < 6; k++) dst[k * nf] = h[k];
         }
@@ -383,16 +384,39 @@ enum SapPhase : int {
 // MAXT / MINB: the launch bounds.  The default form allows 256 threads (an
 // 8x4^3 domain); the occupancy form (128 threads, 3 CTAs per SM) caps the
 // registers at 170 so that three 4^4 domains run on an SM at once.
-// VH: the half-domain size when fixed at compile time (0: taken from the
-// geometry); a fixed size turns the shared-memory offsets of the stencil
-// into immediates.
+// The geometry of a domain shape fixed at compile time (SHAPE 1: 4^4,
+// 2: 8x4^3; 0: taken from the arguments): the volume and the face-slot
+// offsets become immediates in the stencil and the face code.
+template <int SHAPE>
+__device__ __forceinline__ Geom sap_geom(const Geom &g0)
+{
+    Geom g = g0;
+    if (SHAPE > 0) {
+        constexpr int dx = SHAPE == 1 ? 4 : 8, vd = dx * 64;
+        constexpr int fx = vd / dx, fo = vd / 4;  // slots of an x face; of a y, z or t face
+        g.Vd = vd;
+        g.Vh = vd / 2;
+        g.vd_shift = SHAPE == 1 ? 8 : 9;
+        g.nf = 2 * (fx + 3 * fo);
+        g.foff[0] = 0;
+        g.foff[1] = fx;
+        g.foff[2] = 2 * fx;
+        g.foff[3] = 2 * fx + fo;
+        g.foff[4] = 2 * fx + 2 * fo;
+        g.foff[5] = 2 * fx + 3 * fo;
+        g.foff[6] = 2 * fx + 4 * fo;
+        g.foff[7] = 2 * fx + 5 * fo;
+    }
+    return g;
+}
+
 template <typename R, typename SL, typename SC, typename SS, typename SP, bool STL, bool STC, int MAXT = 256,
-          int MINB = 1, int VH = 0>
+          int MINB = 1, int SHAPE = 0>
 __global__ void __launch_bounds__(MAXT, MINB) k_sap(const SapArgs<R, SL, SC, SS, SP> a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
-    const Geom &g = a.g;
-    const int Vd = VH ? 2 * VH : g.Vd, Vh = VH ? VH : g.Vh;
+    const Geom g = sap_geom<SHAPE>(a.g);
+    const int Vd = g.Vd, Vh = g.Vh;
     const int i = threadIdx.x;
     const int bx = blockIdx.x;
     const int d = a.colour * g.Nd2 + a.dfirst + (bx < a.nsplit ? bx : bx + a.dskip);
@@ -461,7 +485,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_sap(const SapArgs<R, SL, SC, SS,
     __shared__ int sNbd[8];
     if (i < 8) sNbd[i] = __ldg(g.nbd + d * 8 + i);
 
-    SapBlock<R, SL, SC, SS, SP, STL, STC> B{a, d, Vd, Vh, sL, sC, sCs};
+    SapBlock<R, SL, SC, SS, SP, STL, STC> B{a, g, d, Vd, Vh, sL, sC, sCs};
     const R kappa = a.kappa;
     const int nwarps = (Vh + 31) / 32;
     const bool full_warps = (Vh % 32) == 0;
@@ -755,12 +779,12 @@ __global__ void __launch_bounds__(128) k_sap_face_apply(const Geom g, const Fiel
 // ---------------------------------------------------------------- launch
 
 template <typename R, typename SL, typename SC, typename SS, typename SP, bool STL, bool STC, int MAXT = 256,
-          int MINB = 1, int VH = 0>
+          int MINB = 1, int SHAPE = 0>
 static qdd_status run_sap(Gauge *g, const SapArgs<R, SL, SC, SS, SP> &a, cudaStream_t s, bool pdl, bool timed)
 {
     const HostGeom &hg = g->hg;
     size_t smem = sap_smem_layout<R, SL, SC>(hg.Vd, STL, STC);
-    auto kern = k_sap<R, SL, SC, SS, SP, STL, STC, MAXT, MINB, VH>;
+    auto kern = k_sap<R, SL, SC, SS, SP, STL, STC, MAXT, MINB, SHAPE>;
     static thread_local size_t configured = 0;
     if (configured < smem) {
         QDD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -824,6 +848,15 @@ static qdd_status dispatch_staging(Gauge *g, const SapArgs<R, SL, SC, SS, SP> &a
     }
     const int Vd = hg.Vd;
     const size_t lim = smem_limit() - 128;  // the kernel's static shared memory
+    int shape = (hg.dom[1] == 4 && hg.dom[2] == 4 && hg.dom[3] == 4) ? (hg.dom[0] == 4 ? 1 : (hg.dom[0] == 8 ? 2 : 0)) : 0;
+    if (shape) {  // the fixed form's constants (sap_geom) must be the geometry's
+        const int fx = Vd / hg.dom[0], fo = Vd / 4;
+        const int foff[8] = {0, fx, 2 * fx, 2 * fx + fo, 2 * fx + 2 * fo, 2 * fx + 3 * fo, 2 * fx + 4 * fo,
+                             2 * fx + 5 * fo};
+        bool same = hg.nf == 2 * (fx + 3 * fo) && hg.Vd == (shape == 1 ? 256 : 512);
+        for (int k = 0; k < 8; k++) same = same && hg.foff[k] == foff[k];
+        if (!same) shape = 0;
+    }
     // the occupancy form: links staged, clover read through the cache, three
     // CTAs per SM (FP32 arithmetic, domains of at most 256 sites)
     if constexpr (sizeof(R) == 4) {
@@ -832,17 +865,17 @@ static qdd_status dispatch_staging(Gauge *g, const SapArgs<R, SL, SC, SS, SP> &a
             return run_sap<R, SL, SC, SS, SP, true, false, 128, 3>(g, a, s, pdl, timed);
     }
     if (sap_smem_layout<R, SL, SC>(Vd, true, true) <= lim) {
-        // 4^4 domains (the 16-bit workloads' shape): the size fixed at compile time
+        // 4^4 domains (the 16-bit workloads' shape): the shape fixed at compile time
         if constexpr (sizeof(R) == 4 && !std::is_same<SL, StF32>::value)
-            if (hg.Vh == 128 && g->sap_variant == 0)
-                return run_sap<R, SL, SC, SS, SP, true, true, 128, 2, 128>(g, a, s, pdl, timed);
+            if (shape == 1 && g->sap_variant == 0)
+                return run_sap<R, SL, SC, SS, SP, true, true, 128, 2, 1>(g, a, s, pdl, timed);
         return run_sap<R, SL, SC, SS, SP, true, true>(g, a, s, pdl, timed);
     }
     if (sap_smem_layout<R, SL, SC>(Vd, true, false) <= lim) {
-        // 8x4^3 domains with FP32 links (the clover does not fit): the size fixed at compile time
+        // 8x4^3 domains with FP32 links (the clover does not fit): the shape fixed at compile time
         if constexpr (sizeof(R) == 4 && std::is_same<SL, StF32>::value)
-            if (hg.Vh == 256 && g->sap_variant == 0)
-                return run_sap<R, SL, SC, SS, SP, true, false, 256, 1, 256>(g, a, s, pdl, timed);
+            if (shape == 2 && g->sap_variant == 0)
+                return run_sap<R, SL, SC, SS, SP, true, false, 256, 1, 2>(g, a, s, pdl, timed);
         return run_sap<R, SL, SC, SS, SP, true, false>(g, a, s, pdl, timed);
     }
     if (sap_smem_layout<R, SL, SC>(Vd, false, false) <= lim)
