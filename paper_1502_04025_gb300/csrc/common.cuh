@@ -264,10 +264,48 @@ __device__ __forceinline__ void reconstruct_add(const cpx<R> *w, cpx<R> *acc)
     }
 }
 
-// w = U h (DAG = false) or U^+ h (DAG = true) for the two spins of h
-template <bool DAG, typename R>
+// FP32 form of su3_mul_half: the two spins of h share every link entry, so
+// their products run as pairs (one paired FMA for the two spins), with the
+// scalar form's order of operations in each lane -- the same bits.
+template <bool DAG>
+__device__ __forceinline__ void su3_mul_half_x2(const cpx<float> *U, const cpx<float> *h, cpx<float> *w)
+{
+    float2 hr[3], hi[3];
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+        hr[b] = make_float2(h[b].re, h[3 + b].re);
+        hi[b] = make_float2(h[b].im, h[3 + b].im);
+    }
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        float2 ar = make_float2(0.f, 0.f), ai = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            const cpx<float> u = DAG ? U[b * 3 + a] : U[a * 3 + b];
+            const float2 ur = make_float2(u.re, u.re);
+            const float2 ui = make_float2(DAG ? u.im : -u.im, DAG ? u.im : -u.im);  // enters re
+            const float2 uj = make_float2(DAG ? -u.im : u.im, DAG ? -u.im : u.im);  // enters im
+            ar = __ffma2_rn(ur, hr[b], ar);
+            ar = __ffma2_rn(ui, hi[b], ar);
+            ai = __ffma2_rn(ur, hi[b], ai);
+            ai = __ffma2_rn(uj, hr[b], ai);
+        }
+        w[a] = mk(ar.x, ai.x);
+        w[3 + a] = mk(ar.y, ai.y);
+    }
+}
+
+// w = U h (DAG = false) or U^+ h (DAG = true) for the two spins of h;
+// PAIRED: the FP32 form runs the two spins as paired FMAs (same bits)
+template <bool DAG, typename R, bool PAIRED = true>
 __device__ __forceinline__ void su3_mul_half(const cpx<R> *U, const cpx<R> *h, cpx<R> *w)
 {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+    if constexpr (sizeof(R) == 4 && PAIRED) {
+        su3_mul_half_x2<DAG>(U, h, w);
+        return;
+    }
+#endif
 #pragma unroll
     for (int sp = 0; sp < 2; sp++)
 #pragma unroll

@@ -269,6 +269,10 @@ qdd_status launch_spinor_out(Gauge *g, const void *src, const float *src_scale, 
 // internal -> internal precision conversion of spinors
 qdd_status launch_spinor_convert(Gauge *g, const void *src, const float *src_scale, qdd_prec sp, void *dst,
                                  float *dst_scale, qdd_prec dp, int nrhs, cudaStream_t s);
+// v = w / |w| (FP64, |w|^2 on the device) and its copy in a 16-bit storage
+// (F16S / BF16S, per-site scale) in one pass, one right-hand side
+qdd_status launch_scale_convert(Gauge *g, const double2 *w, const double2 *norm2, double2 *out64, void *dst,
+                                float *dst_scale, qdd_prec dp, cudaStream_t s);
 // plane-wise down-conversion of links (unscaled) / clover (per-site scale)
 qdd_status launch_links_convert(Gauge *g, qdd_prec dp, void *dst, cudaStream_t s);
 // paired: the full-lattice operator's copy (16-bit formats in paired-plane order)

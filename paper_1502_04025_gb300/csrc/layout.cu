@@ -258,6 +258,41 @@ __global__ void k_spinor_convert(Geom g, Field<SI> src, Field<SO> dst, int64_t r
     store_spinor<SO>(dst, r * rstride, r * sstride, g.Vd, d, s, v);
 }
 
+// v = w / |w| in FP64 (out64, may alias w; |w|^2 from the device) and the
+// same vector in a 16-bit storage with its per-site scale, in one pass: the
+// Arnoldi step's new basis vector and the Schwarz input made from it.  The
+// scaling is the FP64 arithmetic of the plain scaling kernel; the 16-bit copy
+// is rounded from the FP32 value.  One thread per site.
+template <typename SO>
+__global__ void k_scale_convert(Geom g, const double2 *w, const double2 *norm2, double2 *out64, Field<SO> dst)
+{
+    __shared__ double fs;  // once per block: FP64 square root and division are long on the FP64 pipe
+    if (threadIdx.x == 0) {
+        double nn = norm2[0].x;
+        fs = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
+    }
+    __syncthreads();
+    const int gi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi >= g.V) return;
+    int d, s;
+    split_index(g, gi, d, s);
+    const double f = fs;
+    const int64_t base = (int64_t)d * 12 * g.Vd + s;
+    cpx<float> v[12];
+    float m = 0.f;
+    for (int k = 0; k < 12; k++) {
+        double2 a = w[base + (int64_t)k * g.Vd];
+        a = make_double2(a.x * f, a.y * f);
+        out64[base + (int64_t)k * g.Vd] = a;
+        v[k] = mk((float)a.x, (float)a.y);
+        m = fmaxf(m, fmaxf(fabsf(v[k].re), fabsf(v[k].im)));
+    }
+    dst.scale[(int64_t)d * g.Vd + s] = m;
+    const float inv = m > 0.f ? 1.f / m : 0.f;
+    typename SO::T2 *p = dst.p + base;
+    for (int k = 0; k < 12; k++) st_c<float>(p + (int64_t)k * g.Vd, inv * v[k]);
+}
+
 template <typename S>
 __global__ void k_links_convert(int64_t n, const double2 *src, typename S::T2 *dst)
 {
@@ -419,6 +454,26 @@ qdd_status launch_spinor_convert(Gauge *g, const void *src, const float *src_sca
             k_spinor_convert<SI, SO><<<grid, 256, 0, s>>>(g->geom, fi, fo, rs, ss);
         });
     });
+    QDD_CUDA(cudaGetLastError());
+    return QDD_OK;
+}
+
+qdd_status launch_scale_convert(Gauge *g, const double2 *w, const double2 *norm2, double2 *out64, void *dst,
+                                float *dst_scale, qdd_prec dp, cudaStream_t s)
+{
+    const int64_t n = (int64_t)g->hg.V * 12;
+    g->ctx->timer.work(K_BLAS, 2.0 * n, (32.0 + 4.0) * n + 4.0 * g->hg.V);
+    LaunchScope ls(g->ctx->timer, K_BLAS, s);
+    const unsigned grid = (unsigned)((g->hg.V + 127) / 128);
+    if (dp == QDD_PREC_F16S)
+        k_scale_convert<StF16><<<grid, 128, 0, s>>>(g->geom, w, norm2, out64, Field<StF16>{(__half2 *)dst, dst_scale});
+    else if (dp == QDD_PREC_BF16S)
+        k_scale_convert<StBF16><<<grid, 128, 0, s>>>(g->geom, w, norm2, out64,
+                                                     Field<StBF16>{(__nv_bfloat162 *)dst, dst_scale});
+    else {
+        set_error("scale-and-convert takes a 16-bit storage");
+        return QDD_EINVAL;
+    }
     QDD_CUDA(cudaGetLastError());
     return QDD_OK;
 }

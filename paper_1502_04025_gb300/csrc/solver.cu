@@ -221,6 +221,14 @@ qdd_status solve_impl(Gauge *g, Workspace *wsp, const double *b_in, double *x_ou
     // FP32 Schwarz input: written by the scaling that makes v_j, which saves a
     // conversion pass per step (rho_ready: rho holds v_j of every right-hand side)
     float2 *rho32 = (p->use_sap == 1 && spinor_store(sp) == QDD_PREC_F32) ? w.rho.as<float2>() : nullptr;
+    // 16-bit storage: the scaling writes the Schwarz input with its scales too
+    const bool rho16 = p->use_sap == 1 && (sp == QDD_PREC_F16S || sp == QDD_PREC_BF16S);
+    auto scale_v = [&](const double2 *src, int r, const double2 *nrm, double2 *dst) -> qdd_status {
+        if (rho16)
+            return launch_scale_convert(g, src, nrm, dst, (char *)w.rho.p + (size_t)r * n * 4,
+                                        w.rho_s.as<float>() + (size_t)r * g->hg.V, sp, s);
+        return blas_scale_by_norm(ctx, src, n, nrm, dst, s, rho32 ? rho32 + r * n : nullptr);
+    };
     bool rho_ready = false;
     const int kdr = p->dr_k;
     w.hist.clear();
@@ -373,10 +381,8 @@ qdd_status solve_impl(Gauge *g, Workspace *wsp, const double *b_in, double *x_ou
             restarts++;
             deflated++;
         } else {
-            for (int r = 0; r < B; r++)
-                QDD_TRY(blas_scale_by_norm(ctx, R0 + r * n, n, dev + sm.nrm1() + r, V + r * n, s,
-                                           rho32 ? rho32 + r * n : nullptr));
-            rho_ready = rho32 != nullptr;
+            for (int r = 0; r < B; r++) QDD_TRY(scale_v(R0 + r * n, r, dev + sm.nrm1() + r, V + r * n));
+            rho_ready = rho32 != nullptr || rho16;
             for (int r = 0; r < B; r++) {
                 H[r] = dense::Mat(m + 1, m);
                 cv[r].assign(m + 1, zc(0, 0));
@@ -508,8 +514,7 @@ qdd_status solve_impl(Gauge *g, Workspace *wsp, const double *b_in, double *x_ou
                 h(j + 1, j) = hn;
                 // v_{j+1} = w / h_{j+1,j}, with its FP32 copy for the next
                 // preconditioner when every right-hand side goes on
-                QDD_TRY(blas_scale_by_norm(ctx, wv + r * n, n, dev + (two[r] ? sm.nrm2() : sm.nrm1()) + r, wv + r * n,
-                                           s, rho32 ? rho32 + r * n : nullptr));
+                QDD_TRY(scale_v(wv + r * n, r, dev + (two[r] ? sm.nrm2() : sm.nrm1()) + r, wv + r * n));
                 // residual estimate: min |c - Hbar y| over the j+1 columns
                 dense::Mat Hs(j + 2, j + 1);
                 for (int i = 0; i < j + 2; i++)
@@ -522,7 +527,7 @@ qdd_status solve_impl(Gauge *g, Workspace *wsp, const double *b_in, double *x_ou
                 if (est[r] <= p->tol || hn == 0.0) open[r] = 0;
                 all_done = all_done && !open[r];
             }
-            rho_ready = rho32 != nullptr && scaled == B;
+            rho_ready = (rho32 != nullptr || rho16) && scaled == B;
             if (status != QDD_OK || all_done) break;
         }
         if (status != QDD_OK) break;
