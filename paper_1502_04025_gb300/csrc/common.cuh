@@ -348,6 +348,48 @@ __device__ __forceinline__ void herm6_mul(const cpx<R> *blk, const cpx<R> *in, c
         }
 }
 
+// FP32 form of the two clover blocks at once: block 0 (spins 0,1) in lane 0
+// and block 1 (spins 2,3) in lane 1 of paired FMAs.  Each lane runs
+// herm6_mul's sequence of operations, so the result is the same bits.
+__device__ __forceinline__ void herm6_mul_x2(const cpx<float> *b0, const cpx<float> *b1, const cpx<float> *in,
+                                             cpx<float> *out)
+{
+    float2 inr[6], ini[6], ore[6], oim[6];
+#pragma unroll
+    for (int i = 0; i < 6; i++) {
+        inr[i] = make_float2(in[i].re, in[6 + i].re);
+        ini[i] = make_float2(in[i].im, in[6 + i].im);
+    }
+#pragma unroll
+    for (int i = 0; i < 6; i++) {
+        const float2 dd = make_float2((i & 1) ? b0[i >> 1].im : b0[i >> 1].re, (i & 1) ? b1[i >> 1].im : b1[i >> 1].re);
+        ore[i] = __fmul2_rn(dd, inr[i]);
+        oim[i] = __fmul2_rn(dd, ini[i]);
+    }
+    int k = 3;
+#pragma unroll
+    for (int i = 0; i < 6; i++)
+#pragma unroll
+        for (int j = i + 1; j < 6; j++) {
+            const float2 br = make_float2(b0[k].re, b1[k].re), bi = make_float2(b0[k].im, b1[k].im);
+            const float2 nbi = make_float2(-b0[k].im, -b1[k].im);
+            ore[i] = __ffma2_rn(br, inr[j], ore[i]);  // out[i] += b in[j]
+            ore[i] = __ffma2_rn(nbi, ini[j], ore[i]);
+            oim[i] = __ffma2_rn(br, ini[j], oim[i]);
+            oim[i] = __ffma2_rn(bi, inr[j], oim[i]);
+            ore[j] = __ffma2_rn(br, inr[i], ore[j]);  // out[j] += conj(b) in[i]
+            ore[j] = __ffma2_rn(bi, ini[i], ore[j]);
+            oim[j] = __ffma2_rn(br, ini[i], oim[j]);
+            oim[j] = __ffma2_rn(nbi, inr[i], oim[j]);
+            k++;
+        }
+#pragma unroll
+    for (int i = 0; i < 6; i++) {
+        out[i] = mk(ore[i].x, oim[i].x);
+        out[6 + i] = mk(ore[i].y, oim[i].y);
+    }
+}
+
 // ------------------------------------------------------------ double-float
 //
 // A value hi + lo held in two FP32 numbers (|lo| <= ulp(hi)/2), for operator

@@ -189,18 +189,23 @@ struct SapBlock {
     // stored entries
     __device__ __forceinline__ void clover(int s, const cpx<R> *in, cpx<R> *out) const
     {
+        cpx<R> m[2][18];
 #pragma unroll
         for (int blk = 0; blk < 2; blk++) {
-            cpx<R> m[18];
             if (STC) {
 #pragma unroll
-                for (int k = 0; k < 18; k++) m[k] = ld_s<R>(sC + (blk * 18 + k) * Vd + s);
+                for (int k = 0; k < 18; k++) m[blk][k] = ld_s<R>(sC + (blk * 18 + k) * Vd + s);
             } else {
                 const typename SC::T2 *p = a.C.p + ((int64_t)d * 36 + blk * 18) * Vd + s;
 #pragma unroll
-                for (int k = 0; k < 18; k++) m[k] = ld_c<R>(p + (int64_t)k * Vd);
+                for (int k = 0; k < 18; k++) m[blk][k] = ld_c<R>(p + (int64_t)k * Vd);
             }
-            herm6_mul(m, in + 6 * blk, out + 6 * blk);
+        }
+        if constexpr (sizeof(R) == 4) {
+            herm6_mul_x2(m[0], m[1], in, out);  // both blocks in paired FMAs
+        } else {
+            herm6_mul(m[0], in, out);
+            herm6_mul(m[1], in + 6, out + 6);
         }
         if (SC::kScaled) {
             const R sc = STC ? (R)sCs[s] : (R)__ldg(a.C.scale + (int64_t)d * Vd + s);
