@@ -206,15 +206,22 @@ qdd_status qdd_set_link_compression(qdd_gauge *g, int two_rows);
 qdd_status qdd_link_compression(qdd_gauge *g, int *two_rows, int *is_su3);
 
 /*
- * Form of the Schwarz block kernel (the result is the same bits either way):
- * 0 (default) stages the domain's links and, when it fits, its clover in
- * shared memory, with the domain size fixed at compile time for 4^4 domains
- * in 16-bit storage; 1 stages the links only, reads the clover through the
- * cache and is compiled for three CTAs per SM (FP32 arithmetic on domains of
- * at most 256 sites; otherwise form 0 runs); 2 is form 0 with the domain size
- * always taken at run time.  The paper sizes its domains to the cache
- * (Sec. 3.3); on the GPU the choice trades staged data against the number of
- * domains an SM holds.
+ * Form of the Schwarz block kernel.  3 runs two threads per even/odd site
+ * pair, each with two of the four directions and one clover block (FP32
+ * arithmetic, links and clover staged, half a domain a multiple of 32 sites,
+ * at most 512 threads; otherwise the one-thread form of 0 runs); its partial
+ * sums are added in another order, so it agrees with the one-thread form to
+ * rounding.  0 (default) runs form 3 where it applies with FP32 links, and
+ * otherwise one thread per site pair, staging the domain's links and, when
+ * it fits, its clover in shared memory, with the domain size fixed at
+ * compile time for 4^4 domains in 16-bit storage.  1 stages the links only,
+ * reads the clover through the cache and is compiled for three CTAs per SM
+ * (FP32 arithmetic on domains of at most 256 sites; otherwise 0 runs); 2 is
+ * the one-thread form with the domain size always taken at run time.  Forms
+ * 1 and 2 give the same bits as the one-thread form of 0.  The paper sizes
+ * its domains to the cache (Sec. 3.3); on the GPU the choice trades staged
+ * data and registers against the number of warps an SM holds.
+ * Returns QDD_EINVAL for a null field or a form outside 0..3.
  */
 qdd_status qdd_set_schwarz_variant(qdd_gauge *g, int variant);
 

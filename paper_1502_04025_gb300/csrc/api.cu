@@ -495,7 +495,7 @@ qdd_status qdd_check_hits(unsigned long long *hits)
 qdd_status qdd_set_schwarz_variant(qdd_gauge *g, int variant)
 {
     clear_error();
-    if (!g || variant < 0 || variant > 2) {
+    if (!g || variant < 0 || variant > 3) {
         set_error("invalid argument");
         return QDD_EINVAL;
     }

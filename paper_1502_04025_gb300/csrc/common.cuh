@@ -245,10 +245,13 @@ __device__ __forceinline__ void project(const cpx<R> *x, cpx<R> *h)
     }
 }
 
-// acc += (w ; -sgn * a_mu^+ w), w the half spinor after the colour product
-template <int MU, int SGN, typename R>
+// acc += (w ; -sgn * a_mu^+ w), w the half spinor after the colour product.
+// SWAP: acc holds spins (2,3) in its first six entries and spins (0,1) in
+// its last six (the same sums, stored the other way round).
+template <int MU, int SGN, bool SWAP = false, typename R>
 __device__ __forceinline__ void reconstruct_add(const cpx<R> *w, cpx<R> *acc)
 {
+    constexpr int up = SWAP ? 6 : 0, lo = SWAP ? 0 : 6;
 #pragma unroll
     for (int c = 0; c < 3; c++) {
         cpx<R> w0 = w[c], w1 = w[3 + c];
@@ -257,10 +260,10 @@ __device__ __forceinline__ void reconstruct_add(const cpx<R> *w, cpx<R> *acc)
         else if (MU == 1) { b0 = w1; b1 = -w0; }            // i sigma_y w
         else if (MU == 2) { b0 = ti(w0); b1 = tmi(w1); }    // i sigma_z w
         else { b0 = w0; b1 = w1; }
-        acc[0 * 3 + c] = acc[0 * 3 + c] + w0;
-        acc[1 * 3 + c] = acc[1 * 3 + c] + w1;
-        if (SGN > 0) { acc[2 * 3 + c] = acc[2 * 3 + c] - b0; acc[3 * 3 + c] = acc[3 * 3 + c] - b1; }
-        else { acc[2 * 3 + c] = acc[2 * 3 + c] + b0; acc[3 * 3 + c] = acc[3 * 3 + c] + b1; }
+        acc[up + c] = acc[up + c] + w0;
+        acc[up + 3 + c] = acc[up + 3 + c] + w1;
+        if (SGN > 0) { acc[lo + c] = acc[lo + c] - b0; acc[lo + 3 + c] = acc[lo + 3 + c] - b1; }
+        else { acc[lo + c] = acc[lo + c] + b0; acc[lo + 3 + c] = acc[lo + 3 + c] + b1; }
     }
 }
 
@@ -321,13 +324,13 @@ __device__ __forceinline__ void su3_mul_half(const cpx<R> *U, const cpx<R> *h, c
 }
 
 // one hop: acc += (1 - sgn gamma_mu) V x, V = U (forward) or U^+ (backward)
-template <int MU, int SGN, typename R>
+template <int MU, int SGN, bool SWAP = false, typename R>
 __device__ __forceinline__ void hop(const cpx<R> *U, const cpx<R> *x, cpx<R> *acc)
 {
     cpx<R> h[6], w[6];
     project<MU, SGN>(x, h);
     su3_mul_half<(SGN < 0)>(U, h, w);
-    reconstruct_add<MU, SGN>(w, acc);
+    reconstruct_add<MU, SGN, SWAP>(w, acc);
 }
 
 // Hermitian 6x6 block from its packed 18 complex slots

@@ -154,8 +154,18 @@ __device__ __forceinline__ Geom fixed_geom(const Geom &g0)
     return g;
 }
 
+// CTAs per SM the register allocation aims at.  FP16 links: 4 (the lower
+// register cap of 5 costs more in the FP16 and H16 forms: on 32^3x64, FP16
+// 181.5 -> 175.0 us and H16 193.6 -> 190.1 us at 4; FP32 and BF16 are
+// faster at 5, BF16 176.6 against 188.0 us).
+template <typename R, typename SL>
+constexpr int dslash_min_blocks()
+{
+    return sizeof(R) == 4 ? (std::is_same<SL, StF16>::value ? 4 : 5) : 1;
+}
+
 template <typename R, typename SL, typename SC, typename SI, typename SO, bool RESID, bool L12, int VD = 0>
-__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 1) k_dslash(Geom g0, Field<SL> U, Field<SC> A, Field<SI> in, Field<SO> out,
+__global__ void __launch_bounds__(128, (dslash_min_blocks<R, SL>())) k_dslash(Geom g0, Field<SL> U, Field<SC> A, Field<SI> in, Field<SO> out,
                                                 const double2 *b, R kappa)
 {
     const Geom g = fixed_geom<VD>(g0);
@@ -192,10 +202,15 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 1) k_dslash(Geom g0,
                 for (int k = 0; k < 18; k++) m[blk][k] = ld_c<R>(p + (int64_t)(blk * 18 + k) * g.Vd);
             }
         }
-        // (the paired form of the two blocks, kept in the Schwarz kernel, measured
-        // slower here: FP32 256.7 -> 344.0 us on 32^3x64 at this kernel's 96 registers)
-        herm6_mul(m[0], x, y);
-        herm6_mul(m[1], x + 6, y + 6);
+        // The two blocks as paired FMAs (the same bits) only with FP16 clover and
+        // spinors: 175.0 -> 171.9 us on 32^3x64.  Measured slower in the other
+        // forms: FP32 256.7 -> 344.0 us at 96 registers, H16 190.1 -> 198.2 us.
+        if constexpr (std::is_same<SC, StF16>::value && std::is_same<SI, StF16>::value) {
+            herm6_mul_x2(m[0], m[1], x, y);
+        } else {
+            herm6_mul(m[0], x, y);
+            herm6_mul(m[1], x + 6, y + 6);
+        }
         if (SC::kScaled) {  // the clover's per-site scale on the 12 products
 #pragma unroll
             for (int k = 0; k < 12; k++) y[k] = sc * y[k];

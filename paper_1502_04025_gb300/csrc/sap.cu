@@ -214,29 +214,51 @@ struct SapBlock {
         }
     }
 
+    // out = block b (0: spins 0,1; 1: spins 2,3) of C(s) applied to the six
+    // components in (the paired-thread form's share of the clover)
+    __device__ __forceinline__ void clover_blk(int s, int b, const cpx<R> *in, cpx<R> *out) const
+    {
+        static_assert(STC, "the paired-thread form stages the clover");
+        cpx<R> m[18];
+#pragma unroll
+        for (int k = 0; k < 18; k++) m[k] = ld_s<R>(sC + (b * 18 + k) * Vd + s);
+        herm6_mul(m, in, out);
+        if (SC::kScaled) {
+            const R sc = (R)sCs[s];
+#pragma unroll
+            for (int k = 0; k < 6; k++) out[k] = sc * out[k];
+        }
+    }
+
     // hops of site s from a shared-memory half-field (sites src_off..src_off+Vh-1),
-    // dropping hops that leave the domain (Dirichlet boundary)
+    // dropping hops that leave the domain (Dirichlet boundary); ef, eb: the
+    // site's forward and backward neighbour entries in direction MU
+    template <int MU, bool SWAP = false>
+    __device__ __forceinline__ void inner_dir_e(int s, uint16_t ef, uint16_t eb, const cpx<R> *src, int src_off,
+                                                cpx<R> *acc) const
+    {
+        cpx<R> u[9], x[12];
+        if (!(ef & kCross) && QDD_IN_RANGE((ef & kSlotMask) - src_off, 0, Vh)) {
+            int ns = (ef & kSlotMask) - src_off;
+#pragma unroll
+            for (int k = 0; k < 12; k++) x[k] = src[k * Vh + ns];
+            link(d, s, MU, u);
+            hop<MU, +1, SWAP>(u, x, acc);
+        }
+        if (!(eb & kCross) && QDD_IN_RANGE((eb & kSlotMask) - src_off, 0, Vh)) {
+            int ns = eb & kSlotMask;
+#pragma unroll
+            for (int k = 0; k < 12; k++) x[k] = src[k * Vh + ns - src_off];
+            link(d, ns, MU, u);
+            hop<MU, -1, SWAP>(u, x, acc);
+        }
+    }
+
     template <int MU>
     __device__ __forceinline__ void inner_dir(int s, const uint16_t *nb, const cpx<R> *src, int src_off,
                                               cpx<R> *acc) const
     {
-        cpx<R> u[9], x[12];
-        uint16_t e = nb[2 * MU];
-        if (!(e & kCross) && QDD_IN_RANGE((e & kSlotMask) - src_off, 0, Vh)) {
-            int ns = (e & kSlotMask) - src_off;
-#pragma unroll
-            for (int k = 0; k < 12; k++) x[k] = src[k * Vh + ns];
-            link(d, s, MU, u);
-            hop<MU, +1>(u, x, acc);
-        }
-        e = nb[2 * MU + 1];
-        if (!(e & kCross) && QDD_IN_RANGE((e & kSlotMask) - src_off, 0, Vh)) {
-            int ns = e & kSlotMask;
-#pragma unroll
-            for (int k = 0; k < 12; k++) x[k] = src[k * Vh + ns - src_off];
-            link(d, ns, MU, u);
-            hop<MU, -1>(u, x, acc);
-        }
+        inner_dir_e<MU>(s, nb[2 * MU], nb[2 * MU + 1], src, src_off, acc);
     }
 
     // Push the correction dl of site s across the domain faces, into the face
@@ -743,6 +765,289 @@ __global__ void __launch_bounds__(MAXT, MINB) k_sap(const SapArgs<R, SL, SC, SS,
     }
 }
 
+// ------------------------------------------------- paired-thread form
+//
+// The same domain visit with two threads per even/odd site pair (FP32
+// arithmetic, links and clover staged, half-fields of whole warps).  The
+// first Vh threads form half 0, the others half 1 (whole warps, so every
+// branch on the half is uniform in a warp).  Half hb owns clover block hb,
+// i.e. the six components of spins (2hb, 2hb+1) of every vector of the MR
+// iteration, and runs the hops of directions 2hb and 2hb+1.  Its partial
+// hop sum holds all twelve components, its own six first; the other six go
+// to the partner thread through shared memory: in the even phases through
+// the buffer that held the inflowing odd residual (which stays in registers
+// for the visit), in the odd phases through the odd half-field, whose
+// content the previous even phase has consumed.  Face inflow and outflow and
+// the global loads and stores run one site per thread: half 0 the even site,
+// half 1 the odd site.  The kernel runs twice the warps of the one-thread
+// form at under half the registers per thread, so more warps cover each
+// other's shared-memory and arithmetic latencies.  The two partial sums
+// are added last, and the MR dot products run over six components per
+// thread, so results agree with the one-thread form to rounding, not bit
+// for bit.
+template <typename SL, typename SC, typename SS, typename SP, int MAXT, int MINB, int SHAPE>
+__global__ void __launch_bounds__(MAXT, MINB) k_sap_pair(const SapArgs<float, SL, SC, SS, SP> a)
+{
+    using R = float;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const Geom g = sap_geom<SHAPE>(a.g);
+    const int Vd = g.Vd, Vh = g.Vh;
+    const int i = threadIdx.x;
+    const int hb = i >= Vh ? 1 : 0;      // the half (uniform in a warp)
+    const int p = i - hb * Vh;           // the site pair
+    const int mb = 6 * hb, ob = 6 - mb;  // first of the own / the partner's six components
+    const int bx = blockIdx.x;
+    const int d = a.colour * g.Nd2 + a.dfirst + (bx < a.nsplit ? bx : bx + a.dskip);
+    const int se = p, so = Vh + p, sown = hb ? so : se;
+
+    unsigned char *ptr = smem;
+    typename SL::T2 *sL = (typename SL::T2 *)ptr;
+    ptr += align128((size_t)36 * Vd * sizeof(typename SL::T2));
+    typename SC::T2 *sC = (typename SC::T2 *)ptr;
+    ptr += align128((size_t)36 * Vd * sizeof(typename SC::T2));
+    float *sCs = nullptr;
+    if (SC::kScaled) { sCs = (float *)ptr; ptr += align128((size_t)Vd * 4); }
+    cpx<R> *sR = (cpx<R> *)ptr;  ptr += align128((size_t)12 * Vh * sizeof(cpx<R>));  // even half-field
+    cpx<R> *sT = (cpx<R> *)ptr;  ptr += align128((size_t)12 * Vh * sizeof(cpx<R>));  // odd half-field
+    cpx<R> *sX = (cpx<R> *)ptr;  ptr += align128((size_t)12 * Vh * sizeof(cpx<R>));  // rho_o, then exchange
+    R *sRed = (R *)ptr;          ptr += align128((size_t)sap_red_elems(Vh) * sizeof(R));
+    uint64_t *bar = (uint64_t *)ptr;
+    cpx<R> *sF = sT;  // staged face slots, over sT and sX
+    const uint32_t fbytes = (uint32_t)(6 * g.nf * sizeof(cpx<R>));
+    const bool stage_faces = fbytes <= 2 * align128((size_t)12 * Vh * sizeof(cpx<R>));
+
+    if (i == 0) {
+        mbar_init(bar, 1);
+        mbar_init(bar + 1, 1);
+        fence_mbar_init();
+        prefetch_l2(a.rho.p + (int64_t)d * 12 * Vd, (uint32_t)(12 * Vd * sizeof(typename SS::T2)));
+        if (!a.first_psi) prefetch_l2(a.psi.p + (int64_t)d * 12 * Vd, (uint32_t)(12 * Vd * sizeof(typename SP::T2)));
+    }
+    __syncthreads();
+    if (i == 0) {
+        const uint32_t lb = (uint32_t)(36 * Vd * sizeof(typename SL::T2));
+        const uint32_t cb = (uint32_t)(36 * Vd * sizeof(typename SC::T2));
+        const uint32_t sb = SC::kScaled ? (uint32_t)(Vd * 4) : 0;
+        mbar_arrive_expect_tx(bar, lb + cb + sb);
+        bulk_g2s_chunked(sL, a.U.p + (int64_t)d * 36 * Vd, lb, bar);
+        bulk_g2s_chunked(sC, a.C.p + (int64_t)d * 36 * Vd, cb, bar);
+        if (SC::kScaled) bulk_g2s_chunked(sCs, a.C.scale + (int64_t)d * Vd, sb, bar);
+    }
+
+    // the neighbour entries of the two directions of this half, for the
+    // even and the odd site of the pair
+    uint16_t nbe[4], nbo[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        nbe[k] = __ldg(g.nbl + se * 8 + 4 * hb + k);
+        nbo[k] = __ldg(g.nbl + so * 8 + 4 * hb + k);
+    }
+    __shared__ int sNbd[8];
+    if (i < 8) sNbd[i] = __ldg(g.nbd + d * 8 + i);
+
+    SapBlock<R, SL, SC, SS, SP, true, true> B{a, g, d, Vd, Vh, sL, sC, sCs};
+    const R kappa = a.kappa;
+    const int nwarps = 2 * Vh / 32;
+    const int nphase = 3 + 2 * a.nmr;
+
+    // the residual of this thread's site: read before the wait, as in the
+    // one-thread form (written two launches back)
+    cpx<R> v[12];
+    load_sp<R, SS>(a.rho, 0, 0, d, sown, Vd, v);
+    pdl_wait();
+    pdl_launch_dependents();
+    for (int rr = 0; rr < a.nrhs; rr++) {
+        const int64_t rb = rr * a.rstride, sb = rr * a.sstride;
+        if (rr == 0) {
+            bool ok = mbar_wait_bounded(bar, 0, QDD_FIRST_WAIT_SPINS);
+            if (!ok) atomicOr(a.err, kErrMbarTimeout);
+            if (__syncthreads_or(!ok)) {
+                mbar_wait_bounded(bar, 0, 1u << 20);
+                return;
+            }
+        }
+        const int64_t fr = rr * a.fstride;
+        const cpx<R> *fd = a.face + fr + (int64_t)d * 6 * g.nf;
+        const bool hold = a.gather && stage_faces;
+        if (hold) {
+            if (i == 0) {
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(bar + 1, fbytes);
+                bulk_g2s_chunked(sF, fd, fbytes, bar + 1);
+            }
+            bool ok = mbar_wait_bounded(bar + 1, rr & 1, 1u << 22);
+            if (!ok) atomicOr(a.err, kErrMbarTimeout);
+            if (__syncthreads_or(!ok)) {
+                mbar_wait_bounded(bar + 1, rr & 1, 1u << 20);
+                return;
+            }
+            fd = sF;
+        }
+        if (rr > 0) load_sp<R, SS>(a.rho, rb, sb, d, sown, Vd, v);
+        // residual plus the inflow across the faces, one site per thread
+        if (a.gather) {
+            uint16_t nb[8];
+#pragma unroll
+            for (int k = 0; k < 8; k++) nb[k] = __ldg(g.nbl + sown * 8 + k);
+            cpx<R> acc[12];
+            auto lnk = [&](int mu, cpx<R> *u) { B.link(d, sown, mu, u); };
+            face_in(g, nb, __ldg(g.fcoord + sown), fd, lnk, acc);
+#pragma unroll
+            for (int k = 0; k < 12; k++) v[k] = v[k] + kappa * acc[k];
+        }
+        if (hold) __syncthreads();  // every thread has read the staged slots
+        {
+            cpx<R> *dst = hb ? sX : sR;
+#pragma unroll
+            for (int k = 0; k < 12; k++) dst[k * Vh + p] = v[k];
+        }
+        __syncthreads();
+
+        // own components of rho_o (for the whole visit) and of x_e
+        cpx<R> ro[6], x[6];
+#pragma unroll
+        for (int j = 0; j < 6; j++) {
+            ro[j] = sX[(mb + j) * Vh + p];
+            x[j] = mk<R>(0, 0);
+        }
+
+        for (int ph = 0; ph < nphase; ph++) {
+            const int type = ph == 0 ? PH_SETUP_ODD
+                             : ph == 1 ? PH_SETUP_EVEN
+                             : ph == nphase - 1 ? PH_RECON_ODD
+                             : ((ph & 1) ? PH_MR_EVEN : PH_MR_ODD);
+            const int par = (type == PH_SETUP_EVEN || type == PH_MR_EVEN) ? 0 : 1;
+            const int s = par ? so : se;
+
+            // own components of the hop sum from the other parity's half-field
+            cpx<R> hs[6];
+            if (type != PH_SETUP_ODD) {
+                cpx<R> acc[12];  // own six components first
+#pragma unroll
+                for (int k = 0; k < 12; k++) acc[k] = mk<R>(0, 0);
+                const cpx<R> *src = par ? sR : sT;
+                const int off = par ? 0 : Vh;
+                uint16_t e[4];
+#pragma unroll
+                for (int k = 0; k < 4; k++) e[k] = par ? nbo[k] : nbe[k];
+                if (hb == 0) {
+                    B.template inner_dir_e<0>(s, e[0], e[1], src, off, acc);
+                    B.template inner_dir_e<1>(s, e[2], e[3], src, off, acc);
+                } else {
+                    B.template inner_dir_e<2, true>(s, e[0], e[1], src, off, acc);
+                    B.template inner_dir_e<3, true>(s, e[2], e[3], src, off, acc);
+                }
+                cpx<R> *xb = par ? sT : sX;
+#pragma unroll
+                for (int j = 0; j < 6; j++) xb[(ob + j) * Vh + p] = acc[6 + j];
+                __syncthreads();
+#pragma unroll
+                for (int j = 0; j < 6; j++) hs[j] = acc[j] + xb[(mb + j) * Vh + p];
+            } else {
+#pragma unroll
+                for (int j = 0; j < 6; j++) hs[j] = mk<R>(0, 0);
+            }
+
+            if (type == PH_SETUP_EVEN) {
+                // r = rho_e + kappa acc (with nmr = 0 also the final residual, kept in sX)
+#pragma unroll
+                for (int j = 0; j < 6; j++) {
+                    const cpx<R> rj = sR[(mb + j) * Vh + p] + kappa * hs[j];
+                    sR[(mb + j) * Vh + p] = a.nmr > 0 ? rj : x[j];
+                    if (a.nmr == 0) sX[(mb + j) * Vh + p] = rj;
+                }
+                __syncthreads();
+                continue;
+            }
+            cpx<R> r[6];
+            if (type == PH_MR_EVEN) {
+#pragma unroll
+                for (int j = 0; j < 6; j++) r[j] = sR[(mb + j) * Vh + p];
+            }
+            cpx<R> w[6];
+#pragma unroll
+            for (int j = 0; j < 6; j++) {
+                cpx<R> own = type == PH_MR_EVEN ? r[j] : (type == PH_MR_ODD ? mk<R>(0, 0) : ro[j]);
+                R ka = type == PH_MR_EVEN || type == PH_SETUP_ODD ? (R)0 : (type == PH_MR_ODD ? -kappa : kappa);
+                w[j] = own + ka * hs[j];
+            }
+            cpx<R> c[6];
+            B.clover_blk(s, hb, w, c);
+
+            if (type == PH_MR_EVEN) {
+                R pr_re = 0, pr_im = 0, pp = 0;
+#pragma unroll
+                for (int j = 0; j < 6; j++) {
+                    c[j] = c[j] + kappa * hs[j];
+                    pr_re = fma(c[j].re, r[j].re, pr_re);
+                    pr_re = fma(c[j].im, r[j].im, pr_re);
+                    pr_im = fma(c[j].re, r[j].im, pr_im);
+                    pr_im = fma(-c[j].im, r[j].re, pr_im);
+                    pp = fma(c[j].re, c[j].re, pp);
+                    pp = fma(c[j].im, c[j].im, pp);
+                }
+                pr_re = warp_sum(pr_re);
+                pr_im = warp_sum(pr_im);
+                pp = warp_sum(pp);
+                if ((i & 31) == 0 && QDD_IN_RANGE((i >> 5) * 4 + 2, 0, sap_red_elems(Vh))) {
+                    sRed[(i >> 5) * 4 + 0] = pr_re;
+                    sRed[(i >> 5) * 4 + 1] = pr_im;
+                    sRed[(i >> 5) * 4 + 2] = pp;
+                }
+                __syncthreads();
+                R tr = 0, ti_ = 0, tp = 0;
+                for (int wv = 0; wv < nwarps; wv++) {
+                    tr += sRed[wv * 4 + 0];
+                    ti_ += sRed[wv * 4 + 1];
+                    tp += sRed[wv * 4 + 2];
+                }
+                const cpx<R> alpha = tp > (R)0 ? mk<R>(tr / tp, ti_ / tp) : mk<R>(0, 0);
+                const bool last = ph == nphase - 2;
+#pragma unroll
+                for (int j = 0; j < 6; j++) {
+                    cfma(x[j], alpha, r[j]);
+                    r[j] = r[j] - alpha * c[j];
+                    sR[(mb + j) * Vh + p] = last ? x[j] : r[j];
+                    if (last) sX[(mb + j) * Vh + p] = r[j];  // the final residual
+                }
+            } else {
+                // setup-odd / mr-odd: t_o; reconstruction: x_o (own components)
+#pragma unroll
+                for (int j = 0; j < 6; j++) sT[(mb + j) * Vh + p] = c[j];
+            }
+            __syncthreads();
+        }
+
+        // outputs of the visit, one site per thread: the correction delta
+        // (x_e in sR, x_o in sT) pushed across the faces, psi += delta; the
+        // residual: the final MR residual (in sX) on the even site, zero on
+        // the odd site
+        {
+            const cpx<R> *src = hb ? sT : sR;
+            cpx<R> dl[12];
+#pragma unroll
+            for (int k = 0; k < 12; k++) dl[k] = src[k * Vh + p];
+            uint16_t nb[8];
+#pragma unroll
+            for (int k = 0; k < 8; k++) nb[k] = __ldg(g.nbl + sown * 8 + k);
+            B.face_out(sown, nb, __ldg(g.fcoord + sown), sNbd, dl, a.face + fr);
+            if (a.first_psi) {
+                store_sp<R, SP>(a.psi, rb, sb, d, sown, Vd, dl);
+            } else {
+                cpx<R> q[12];
+                load_sp<R, SP>(a.psi, rb, sb, d, sown, Vd, q);
+#pragma unroll
+                for (int k = 0; k < 12; k++) q[k] = q[k] + dl[k];
+                store_sp<R, SP>(a.psi, rb, sb, d, sown, Vd, q);
+            }
+#pragma unroll
+            for (int k = 0; k < 12; k++) dl[k] = hb ? mk<R>(0, 0) : sX[k * Vh + p];
+            store_sp<R, SS>(a.rho, rb, sb, d, sown, Vd, dl);
+        }
+        if (rr + 1 < a.nrhs) __syncthreads();  // sR, sT and sX are restaged for the next source
+    }
+}
+
 // ------------------------------------------------------------ face inflow
 //
 // Applies the pending face slots of the domains of one colour to their
@@ -813,6 +1118,35 @@ static qdd_status run_sap(Gauge *g, const SapArgs<R, SL, SC, SS, SP> &a, cudaStr
     return QDD_OK;
 }
 
+template <typename SL, typename SC, typename SS, typename SP, int MAXT, int MINB, int SHAPE>
+static qdd_status run_sap_pair(Gauge *g, const SapArgs<float, SL, SC, SS, SP> &a, cudaStream_t s, bool pdl,
+                               bool timed)
+{
+    const HostGeom &hg = g->hg;
+    size_t smem = sap_smem_layout<float, SL, SC>(hg.Vd, true, true);
+    auto kern = k_sap_pair<SL, SC, SS, SP, MAXT, MINB, SHAPE>;
+    static thread_local size_t configured = 0;
+    if (configured < smem) {
+        QDD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        QDD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      (int)cudaSharedmemCarveoutMaxShared));
+        configured = smem;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(a.nblocks);
+    cfg.blockDim = dim3(2 * hg.Vh);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    LaunchScope ls(g->ctx->timer, K_SAP, s, timed);
+    QDD_CUDA(cudaLaunchKernelEx(&cfg, kern, a));
+    return QDD_OK;
+}
+
 static size_t smem_limit()
 {
     static size_t lim = 0;
@@ -868,6 +1202,21 @@ static qdd_status dispatch_staging(Gauge *g, const SapArgs<R, SL, SC, SS, SP> &a
         if (g->sap_variant == 1 && hg.Vh <= 128 && 3 * (sap_smem_layout<R, SL, SC>(Vd, true, false) + 128) <= 3 * lim &&
             3 * (sap_smem_layout<R, SL, SC>(Vd, true, false) + 1024) <= smem_per_sm())
             return run_sap<R, SL, SC, SS, SP, true, false, 128, 3>(g, a, s, pdl, timed);
+    }
+    // the paired-thread form: FP32 arithmetic, links and clover staged,
+    // half-fields of whole warps, at most 512 threads.  The default with FP32
+    // links, where the one-thread form runs one CTA of Vh threads per SM (4^4
+    // domains, 32^3x64: 0.675 against 0.927 ms per half-sweep); with 16-bit
+    // links two one-thread CTAs share an SM and the paired form, with more
+    // instructions per site, is no faster (48^3x96 BF16: 2.40 against 2.30 ms).
+    if constexpr (sizeof(R) == 4) {
+        const bool pair = g->sap_variant == 3 || (g->sap_variant == 0 && std::is_same<SL, StF32>::value);
+        if (pair && hg.Vh % 32 == 0 && 2 * hg.Vh <= 512 && sap_smem_layout<R, SL, SC>(Vd, true, true) <= lim) {
+            constexpr int kMinb = sizeof(typename SL::T2) == 4 ? 2 : 1;  // 16-bit: two 4^4 domains per SM
+            if (shape == 1) return run_sap_pair<SL, SC, SS, SP, 256, kMinb, 1>(g, a, s, pdl, timed);
+            if (shape == 2) return run_sap_pair<SL, SC, SS, SP, 512, 1, 2>(g, a, s, pdl, timed);
+            return run_sap_pair<SL, SC, SS, SP, 512, 1, 0>(g, a, s, pdl, timed);
+        }
     }
     if (sap_smem_layout<R, SL, SC>(Vd, true, true) <= lim) {
         // 4^4 domains (the 16-bit workloads' shape): the shape fixed at compile time

@@ -310,8 +310,10 @@ def qdd_check_hits() -> int:
 
 def qdd_set_schwarz_variant(g, variant: int):
     """0: links and clover staged when they fit (domain size fixed at compile
-    time for 16-bit 4^4 domains); 1: links staged, clover through the cache,
-    three CTAs per SM; 2: form 0 with the size taken at run time (same results)."""
+    time for 16-bit 4^4 domains; form 3 with FP32 links); 1: links staged,
+    clover through the cache, three CTAs per SM; 2: the one-thread form with
+    the size taken at run time; 3: two threads per site pair (FP32
+    arithmetic; agrees with the one-thread form to rounding)."""
     _check(_lib.qdd_set_schwarz_variant(g, int(variant)), "qdd_set_schwarz_variant")
 
 
