@@ -148,6 +148,14 @@ struct SapArgs {
     int dfirst, nsplit, dskip, nblocks;  // nblocks: the grid
 };
 
+// block b's domain in a launch
+template <typename A>
+__device__ __forceinline__ int sap_domain(const A &a, int Nd2, int b)
+{
+    return a.colour * Nd2 + a.dfirst + (b < a.nsplit ? b : b + a.dskip);
+}
+
+
 __host__ __device__ constexpr size_t align128(size_t b) { return (b + 127) & ~(size_t)127; }
 
 // entries of the MR reduction buffer: 4 per warp when the half-field fills
@@ -446,7 +454,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_sap(const SapArgs<R, SL, SC, SS,
     const int Vd = g.Vd, Vh = g.Vh;
     const int i = threadIdx.x;
     const int bx = blockIdx.x;
-    const int d = a.colour * g.Nd2 + a.dfirst + (bx < a.nsplit ? bx : bx + a.dskip);
+    const int d = sap_domain(a, g.Nd2, bx);
     const int se = i, so = Vh + i;
 
     unsigned char *ptr = smem;
@@ -797,7 +805,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_sap_pair(const SapArgs<float, SL
     const int p = i - hb * Vh;           // the site pair
     const int mb = 6 * hb, ob = 6 - mb;  // first of the own / the partner's six components
     const int bx = blockIdx.x;
-    const int d = a.colour * g.Nd2 + a.dfirst + (bx < a.nsplit ? bx : bx + a.dskip);
+    const int d = sap_domain(a, g.Nd2, bx);
     const int se = p, so = Vh + p, sown = hb ? so : se;
 
     unsigned char *ptr = smem;
