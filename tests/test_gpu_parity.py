@@ -337,6 +337,27 @@ def test_solve_plain_gmres_and_multi_rhs(q, ctx, ora):
     assert rep0["iters"] > rep["iters"]
 
 
+def test_solve_from_page_locked_host_buffers(q, ctx, ora):
+    """Host buffers, pageable or page-locked (the bench's end-to-end case),
+    give the same bits, also in place (the solution written over the
+    source); the source is read only."""
+    import torch
+
+    P = problem(q, ctx, ora, (8, 8, 8, 8), (4, 4, 4, 4))
+    b = np.ascontiguousarray(inputs.gaussian_source(P.L, 2001, nrhs=2))
+    x_staged, rep = q.qdd_solve(P.g, b, tol=1e-10, nrhs=2, sap_prec="f32")
+    bp = torch.from_numpy(b).pin_memory()
+    xp = torch.zeros_like(bp).pin_memory()
+    x_mapped, rep2 = q.qdd_solve(P.g, bp.numpy(), x=xp.numpy(), tol=1e-10, nrhs=2, sap_prec="f32")
+    assert rep["converged"] and rep2["iters"] == rep["iters"]
+    assert np.array_equal(x_mapped, x_staged) and np.array_equal(xp.numpy(), x_staged)
+    assert np.array_equal(bp.numpy(), b)  # the source is read only
+    q.qdd_solve(P.g, bp.numpy(), x=bp.numpy(), tol=1e-10, nrhs=2, sap_prec="f32")
+    assert np.array_equal(bp.numpy(), x_staged)
+    for r in range(2):
+        assert _true_rel(ora, P, x_mapped[r], b[r]) <= 1e-10
+
+
 def test_cdot_multi_matches_numpy(q, ctx):
     import torch
 
