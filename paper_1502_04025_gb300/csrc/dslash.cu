@@ -22,6 +22,18 @@
 
 namespace qdd {
 
+// FP16 spinors (quad planes): site s of the domain block at blk_base, scaled
+template <typename R, typename S>
+__device__ __forceinline__ void load_spinor_quad(const Field<S> &f, int64_t blk_base, int s, int64_t sidx, int Vd,
+                                                 cpx<R> *x)
+{
+    const R sc = (R)__ldg(f.scale + sidx);
+    ld_sp_site<R, S>(f.p + blk_base, s, Vd, x);
+#pragma unroll
+    for (int k = 0; k < 12; k++) x[k] = sc * x[k];
+}
+
+// spinors in planes: the site's first component at gi_plane_base
 template <typename R, typename S>
 __device__ __forceinline__ void load_spinor(const Field<S> &f, int64_t gi_plane_base, int64_t sidx, int Vd,
                                             cpx<R> *x)
@@ -96,7 +108,17 @@ __device__ __forceinline__ void hop_scaled(const cpx<R> *U, const cpx<R> *x, R s
     reconstruct_add<MU, SGN>(w, acc);
 }
 
-// the unscaled components of a spinor and, for a 16-bit field, its scale
+// the unscaled components of a spinor and, for a 16-bit field, its scale;
+// fields in planes: the site's first component at gi_plane_base; FP16 fields
+// (quad planes): site s of the domain block at blk_base
+template <typename R, typename S>
+__device__ __forceinline__ R load_spinor_raw_quad(const Field<S> &f, int64_t blk_base, int s, int64_t sidx, int Vd,
+                                                  cpx<R> *x)
+{
+    ld_sp_site<R, S>(f.p + blk_base, s, Vd, x);
+    return (R)__ldg(f.scale + sidx);
+}
+
 template <typename R, typename S>
 __device__ __forceinline__ R load_spinor_raw(const Field<S> &f, int64_t gi_plane_base, int64_t sidx, int Vd,
                                              cpx<R> *x)
@@ -120,8 +142,13 @@ __device__ __forceinline__ void dslash_dir(const Geom &g, const Field<SL> &U, co
         int nd = (e & kCross) ? __ldg(g.nbd + d * 8 + 2 * MU) : d;
         int ns = e & kSlotMask;
         if (QDD_IN_RANGE(nd, 0, g.Nd) && QDD_IN_RANGE(ns, 0, g.Vd)) {
-            R sc = load_spinor_raw<R, SI>(in, rbase + (int64_t)nd * 12 * g.Vd + ns, sbase + (int64_t)nd * g.Vd + ns,
-                                          g.Vd, x);
+            R sc;
+            if constexpr (SI::kQuad)
+                sc = load_spinor_raw_quad<R, SI>(in, rbase + (int64_t)nd * 12 * g.Vd, ns,
+                                                 sbase + (int64_t)nd * g.Vd + ns, g.Vd, x);
+            else
+                sc = load_spinor_raw<R, SI>(in, rbase + (int64_t)nd * 12 * g.Vd + ns, sbase + (int64_t)nd * g.Vd + ns,
+                                            g.Vd, x);
             load_link<R, SL, L12>(U, d, s, MU, g.Vd, u);
             hop_scaled<MU, +1, SI::kScaled, kPaired>(u, x, sc, acc);
         }
@@ -131,8 +158,13 @@ __device__ __forceinline__ void dslash_dir(const Geom &g, const Field<SL> &U, co
         int nd = (e & kCross) ? __ldg(g.nbd + d * 8 + 2 * MU + 1) : d;
         int ns = e & kSlotMask;
         if (QDD_IN_RANGE(nd, 0, g.Nd) && QDD_IN_RANGE(ns, 0, g.Vd)) {
-            R sc = load_spinor_raw<R, SI>(in, rbase + (int64_t)nd * 12 * g.Vd + ns, sbase + (int64_t)nd * g.Vd + ns,
-                                          g.Vd, x);
+            R sc;
+            if constexpr (SI::kQuad)
+                sc = load_spinor_raw_quad<R, SI>(in, rbase + (int64_t)nd * 12 * g.Vd, ns,
+                                                 sbase + (int64_t)nd * g.Vd + ns, g.Vd, x);
+            else
+                sc = load_spinor_raw<R, SI>(in, rbase + (int64_t)nd * 12 * g.Vd + ns, sbase + (int64_t)nd * g.Vd + ns,
+                                            g.Vd, x);
             load_link<R, SL, L12>(U, nd, ns, MU, g.Vd, u);
             hop_scaled<MU, -1, SI::kScaled, kPaired>(u, x, sc, acc);
         }
@@ -185,7 +217,10 @@ __global__ void __launch_bounds__(128, (dslash_min_blocks<R, SL>())) k_dslash(Ge
     dslash_dir<3, R, SL, SI, L12>(g, U, in, rbase, sbase, d, s, acc);
 
     cpx<R> x[12];
-    load_spinor<R, SI>(in, rbase + (int64_t)d * 12 * g.Vd + s, sbase + gi, g.Vd, x);
+    if constexpr (SI::kQuad)
+        load_spinor_quad<R, SI>(in, rbase + (int64_t)d * 12 * g.Vd, s, sbase + gi, g.Vd, x);
+    else
+        load_spinor<R, SI>(in, rbase + (int64_t)d * 12 * g.Vd + s, sbase + gi, g.Vd, x);
     cpx<R> y[12];
     {
         const typename SC::T2 *p = A.p + (int64_t)d * 36 * g.Vd + s;
@@ -237,8 +272,14 @@ __global__ void __launch_bounds__(128, (dslash_min_blocks<R, SL>())) k_dslash(Ge
         float scf = (float)m;
         out.scale[sbase + gi] = scf;
         R inv = m > 0 ? (R)1 / (R)scf : (R)0;
+        if constexpr (SO::kQuad) {
 #pragma unroll
-        for (int k = 0; k < 12; k++) st_c<R>(op + (int64_t)k * g.Vd, inv * y[k]);
+            for (int k = 0; k < 12; k++) y[k] = inv * y[k];
+            st_sp_site<R, SO>(out.p + rbase + (int64_t)d * 12 * g.Vd, s, g.Vd, y);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 12; k++) st_c<R>(op + (int64_t)k * g.Vd, inv * y[k]);
+        }
     } else {
 #pragma unroll
         for (int k = 0; k < 12; k++) st_c<R>(op + (int64_t)k * g.Vd, y[k]);

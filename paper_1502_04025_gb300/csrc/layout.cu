@@ -187,7 +187,13 @@ __device__ __forceinline__ void store_spinor(Field<S> f, int64_t base, int64_t s
         float sc = (float)m;
         double inv = m > 0 ? 1.0 / (double)sc : 0.0;
         f.scale[sbase + (int64_t)d * Vd + s] = sc;
-        for (int k = 0; k < 12; k++) st_c<double>(p + (int64_t)k * Vd, mk(v[k].re * inv, v[k].im * inv));
+        if constexpr (S::kQuad) {
+            cpx<double> y[12];
+            for (int k = 0; k < 12; k++) y[k] = mk(v[k].re * inv, v[k].im * inv);
+            st_sp_site<double, S>(f.p + base + (int64_t)d * 12 * Vd, s, Vd, y);
+        } else {
+            for (int k = 0; k < 12; k++) st_c<double>(p + (int64_t)k * Vd, mk(v[k].re * inv, v[k].im * inv));
+        }
     } else {
         for (int k = 0; k < 12; k++) st_c<double>(p + (int64_t)k * Vd, v[k]);
     }
@@ -197,9 +203,15 @@ template <typename S>
 __device__ __forceinline__ void load_spinor_d(Field<S> f, int64_t base, int64_t sbase, int Vd, int d, int s,
                                               cpx<double> *v)
 {
-    const typename S::T2 *p = f.p + base + (int64_t)d * 12 * Vd + s;
-    double sc = S::kScaled ? (double)f.scale[sbase + (int64_t)d * Vd + s] : 1.0;
-    for (int k = 0; k < 12; k++) v[k] = sc * ld_c<double>(p + (int64_t)k * Vd);
+    if constexpr (S::kQuad) {
+        double sc = (double)f.scale[sbase + (int64_t)d * Vd + s];
+        ld_sp_site<double, S>(f.p + base + (int64_t)d * 12 * Vd, s, Vd, v);
+        for (int k = 0; k < 12; k++) v[k] = sc * v[k];
+    } else {
+        const typename S::T2 *p = f.p + base + (int64_t)d * 12 * Vd + s;
+        double sc = S::kScaled ? (double)f.scale[sbase + (int64_t)d * Vd + s] : 1.0;
+        for (int k = 0; k < 12; k++) v[k] = sc * ld_c<double>(p + (int64_t)k * Vd);
+    }
 }
 
 __global__ void k_links_in(Geom g, const int *site_of, const double2 *src, double2 *dst)
@@ -289,8 +301,13 @@ __global__ void k_scale_convert(Geom g, const double2 *w, const double2 *norm2, 
     }
     dst.scale[(int64_t)d * g.Vd + s] = m;
     const float inv = m > 0.f ? 1.f / m : 0.f;
-    typename SO::T2 *p = dst.p + base;
-    for (int k = 0; k < 12; k++) st_c<float>(p + (int64_t)k * g.Vd, inv * v[k]);
+    if constexpr (SO::kQuad) {
+        for (int k = 0; k < 12; k++) v[k] = inv * v[k];
+        st_sp_site<float, SO>(dst.p + (int64_t)d * 12 * g.Vd, s, g.Vd, v);
+    } else {
+        typename SO::T2 *p = dst.p + base;
+        for (int k = 0; k < 12; k++) st_c<float>(p + (int64_t)k * g.Vd, inv * v[k]);
+    }
 }
 
 template <typename S>

@@ -366,12 +366,19 @@ __device__ __forceinline__ void face_in(const Geom &g, const uint16_t *nb, uint3
 template <typename R, typename S>
 __device__ __forceinline__ void load_sp(const Field<S> &f, int64_t rb, int64_t sb, int d, int s, int Vd, cpx<R> *x)
 {
-    const typename S::T2 *p = f.p + rb + (int64_t)d * 12 * Vd + s;
-    R sc = S::kScaled ? (R)f.scale[sb + (int64_t)d * Vd + s] : (R)1;
+    if constexpr (S::kQuad) {
+        R sc = (R)f.scale[sb + (int64_t)d * Vd + s];
+        ld_sp_site<R, S, false>(f.p + rb + (int64_t)d * 12 * Vd, s, Vd, x);
 #pragma unroll
-    for (int k = 0; k < 12; k++) {
-        cpx<R> v = ld_s<R>(p + (int64_t)k * Vd);
-        x[k] = S::kScaled ? sc * v : v;
+        for (int k = 0; k < 12; k++) x[k] = sc * x[k];
+    } else {
+        const typename S::T2 *p = f.p + rb + (int64_t)d * 12 * Vd + s;
+        R sc = S::kScaled ? (R)f.scale[sb + (int64_t)d * Vd + s] : (R)1;
+#pragma unroll
+        for (int k = 0; k < 12; k++) {
+            cpx<R> v = ld_s<R>(p + (int64_t)k * Vd);
+            x[k] = S::kScaled ? sc * v : v;
+        }
     }
 }
 
@@ -387,8 +394,15 @@ __device__ __forceinline__ void store_sp(const Field<S> &f, int64_t rb, int64_t 
         float sc = (float)m;
         f.scale[sb + (int64_t)d * Vd + s] = sc;
         R inv = m > 0 ? (R)1 / (R)sc : (R)0;
+        if constexpr (S::kQuad) {
+            cpx<R> y[12];
 #pragma unroll
-        for (int k = 0; k < 12; k++) st_c<R>(p + (int64_t)k * Vd, inv * x[k]);
+            for (int k = 0; k < 12; k++) y[k] = inv * x[k];
+            st_sp_site<R, S>(f.p + rb + (int64_t)d * 12 * Vd, s, Vd, y);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 12; k++) st_c<R>(p + (int64_t)k * Vd, inv * x[k]);
+        }
     } else {
 #pragma unroll
         for (int k = 0; k < 12; k++) st_c<R>(p + (int64_t)k * Vd, x[k]);
