@@ -89,6 +89,12 @@ def parse():
     ap.add_argument("--serve-in-line", type=int, default=100,
                     help="requests of the serving mix reported in the solve line (0 = none)")
     ap.add_argument("--op-bench", action="store_true", help="time only the full-lattice operator")
+    ap.add_argument("--sap-bench", action="store_true",
+                    help="time only the Schwarz preconditioner (nmr 4, 8 half-sweeps per application)")
+    ap.add_argument("--sap-lattice", default="24,24,24,48")
+    ap.add_argument("--sap-precs", default="bf16")
+    ap.add_argument("--sap-iters", type=int, default=5)
+    ap.add_argument("--sap-form", type=int, default=0, help="qdd_set_schwarz_variant form (0: the default)")
     ap.add_argument("--mg", action="store_true",
                     help="time-to-solution near the critical kappa: Schwarz-only against the two-level multigrid")
     ap.add_argument("--op-lattice", default="32,32,32,64")
@@ -754,6 +760,56 @@ def run_op_bench(args):
     qdd.qdd_destroy(ctx)
 
 
+def run_sap_bench(args):
+    """The Schwarz preconditioner alone (the headline workload's parameters:
+    eps 0.7, c_sw 1.5, kappa 0.1355, 4^4 domains, nmr 4, 8 half-sweeps per
+    application) on one lattice, per storage precision: 3 applications
+    untimed, then --sap-iters event-timed.  A small lattice (the default,
+    24^3x48, 1296 domains per colour) is the case the Schwarz kernel's ncu
+    captures run on."""
+    import torch
+
+    from paper_1502_04025_gb300 import build, inputs
+
+    build.build()
+    from paper_1502_04025_gb300 import qdd
+
+    pk, pk_kind = peaks()
+    sm_count = torch.cuda.get_device_properties(0).multi_processor_count
+    fp32_peak = sm_count * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12  # TFLOP/s
+    L = tuple(int(v) for v in args.sap_lattice.split(","))
+    W = CONFIGS[4]
+    ctx = qdd.qdd_create(0, 0)
+    U = inputs.gauge_field(L, W["eps"], 1003)
+    g = qdd.qdd_create_gauge_field(ctx, L, W["dom"], U)
+    del U
+    qdd.qdd_set_clover(g, W["csw"], W["kappa"])
+    qdd.qdd_set_schwarz_variant(g, args.sap_form)
+    eta = torch.from_numpy(inputs.gaussian_source(L, 2003)).cuda()
+    V = int(np.prod(L))
+    flop = sap_flop_per_site(W["dom"], W["nmr"]) * V / 2  # one half-sweep: half the sites' domains
+    out = {"metric": "Schwarz half-sweep time", "unit": "ms", "lattice": list(L), "domain": list(W["dom"]),
+           "nmr": W["nmr"], "form": args.sap_form, "peak_fp32_tflops": fp32_peak,
+           "peak_kind": "of measured" if pk_kind == "measured" else "of fallback"}
+    for prec in args.sap_precs.split(","):
+        for _ in range(3):
+            qdd.qdd_sap_apply(g, eta, W["nmr"], 8, prec)
+        torch.cuda.synchronize()
+        qdd.qdd_set_profiling(ctx, qdd.QDD_PROF_SAP)
+        qdd.qdd_get_kernel_times(ctx, reset=True)
+        for _ in range(args.sap_iters):
+            qdd.qdd_sap_apply(g, eta, W["nmr"], 8, prec)
+        torch.cuda.synchronize()
+        kt = qdd.qdd_get_kernel_times(ctx, reset=True)
+        qdd.qdd_set_profiling(ctx, 0)
+        ms = kt["sap"][0] / kt["sap"][1]
+        out[prec] = {"ms_per_half_sweep": ms, "launches": kt["sap"][1],
+                     "tflops": flop / (ms * 1e-3) / 1e12, "frac_fp32": flop / (ms * 1e-3) / 1e12 / fp32_peak}
+    print(json.dumps(out), flush=True)
+    qdd.qdd_destroy_gauge(g)
+    qdd.qdd_destroy(ctx)
+
+
 # ------------------------------------------------------------ multigrid
 
 MGW = dict(L=(16, 16, 16, 32), dom=(8, 4, 4, 4), eps=0.5, csw=1.0, kappa=0.143, gauge_seed=1002, source_seed=2002,
@@ -961,6 +1017,8 @@ def main():
         run_serve(args)
     elif args.op_bench:
         run_op_bench(args)
+    elif args.sap_bench:
+        run_sap_bench(args)
     elif args.mg:
         run_mg_bench(args)
     else:
