@@ -418,6 +418,28 @@ __device__ __forceinline__ void su3_mul_half(const cpx<R> *U, const cpx<R> *h, c
 }
 
 // one hop: acc += (1 - sgn gamma_mu) V x, V = U (forward) or U^+ (backward)
+// reconstruct_add with a weight m (1: the same sums, as single-rounded
+// fused multiply-adds of 1 * w; 0: acc unchanged), for hops that every lane
+// evaluates and only some keep
+template <int MU, int SGN, typename R>
+__device__ __forceinline__ void reconstruct_fma(R m, const cpx<R> *w, cpx<R> *acc)
+{
+    const R ms = SGN > 0 ? -m : m;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        cpx<R> w0 = w[c], w1 = w[3 + c];
+        cpx<R> b0, b1;  // a^+ w
+        if (MU == 0) { b0 = ti(w1); b1 = ti(w0); }
+        else if (MU == 1) { b0 = w1; b1 = -w0; }
+        else if (MU == 2) { b0 = ti(w0); b1 = tmi(w1); }
+        else { b0 = w0; b1 = w1; }
+        acc[c] = mk<R>(fma(m, w0.re, acc[c].re), fma(m, w0.im, acc[c].im));
+        acc[3 + c] = mk<R>(fma(m, w1.re, acc[3 + c].re), fma(m, w1.im, acc[3 + c].im));
+        acc[6 + c] = mk<R>(fma(ms, b0.re, acc[6 + c].re), fma(ms, b0.im, acc[6 + c].im));
+        acc[9 + c] = mk<R>(fma(ms, b1.re, acc[9 + c].re), fma(ms, b1.im, acc[9 + c].im));
+    }
+}
+
 template <int MU, int SGN, bool SWAP = false, typename R>
 __device__ __forceinline__ void hop(const cpx<R> *U, const cpx<R> *x, cpx<R> *acc)
 {
