@@ -3,7 +3,9 @@
 // after an MR block solve, here the kernel boundary).
 //
 // One CTA per domain Lambda of the colour being swept, one thread per
-// even/odd site pair.  The domain's links and Schwarz clover blocks (A on even
+// even/odd site pair (k_sap), or two threads per site pair, each with two of
+// the four directions and one clover block (k_sap_pair, the form for FP32
+// links; see there).  The domain's links and Schwarz clover blocks (A on even
 // sites, A^{-1} on odd sites) are staged into shared memory with bulk async
 // copies (cp.async.bulk, completion on an mbarrier) when they fit; Sec. 3.3
 // keeps each domain resident in a core's L2 for the same reason.  Then:
@@ -886,11 +888,16 @@ __global__ void __launch_bounds__(MAXT, MINB) k_sap(const SapArgs<R, SL, SC, SS,
 // content the previous even phase has consumed.  Face inflow and outflow and
 // the global loads and stores run one site per thread: half 0 the even site,
 // half 1 the odd site.  The kernel runs twice the warps of the one-thread
-// form at under half the registers per thread, so more warps cover each
-// other's shared-memory and arithmetic latencies.  The two partial sums
-// are added last, and the MR dot products run over six components per
-// thread, so results agree with the one-thread form to rounding, not bit
-// for bit.
+// form in the same shared memory, at 128 registers per thread, so more
+// warps cover each other's shared-memory and arithmetic latencies; it also
+// executes more instructions per site (each thread's clover block in scalar
+// FMAs, the exchange).  With FP32 links, where the one-thread form holds a
+// single 4-warp CTA per SM, that pays (32^3x64: 0.647 against 0.927 ms per
+// half-sweep); with 16-bit links, two one-thread CTAs share an SM and the
+// paired form is not faster (48^3x96 BF16: 2.40 against 2.29 ms).  The two
+// partial sums are added last, and the MR dot products run over six
+// components per thread, so results agree with the one-thread form to
+// rounding, not bit for bit.
 template <typename SL, typename SC, typename SS, typename SP, int MAXT, int MINB, int SHAPE>
 __global__ void __launch_bounds__(MAXT, MINB) k_sap_pair(const SapArgs<float, SL, SC, SS, SP> a)
 {
@@ -1315,9 +1322,9 @@ static qdd_status dispatch_staging(Gauge *g, const SapArgs<R, SL, SC, SS, SP> &a
     // the paired-thread form: FP32 arithmetic, links and clover staged,
     // half-fields of whole warps, at most 512 threads.  The default with FP32
     // links, where the one-thread form runs one CTA of Vh threads per SM (4^4
-    // domains, 32^3x64: 0.675 against 0.927 ms per half-sweep); with 16-bit
+    // domains, 32^3x64: 0.647 against 0.927 ms per half-sweep); with 16-bit
     // links two one-thread CTAs share an SM and the paired form, with more
-    // instructions per site, is no faster (48^3x96 BF16: 2.40 against 2.30 ms).
+    // instructions per site, is no faster (48^3x96 BF16: 2.40 against 2.29 ms).
     if constexpr (sizeof(R) == 4) {
         const bool pair = g->sap_variant == 3 || (g->sap_variant == 0 && std::is_same<SL, StF32>::value);
         if (pair && hg.Vh % 32 == 0 && 2 * hg.Vh <= 512 && sap_smem_layout<R, SL, SC>(Vd, true, true) <= lim) {
