@@ -83,3 +83,26 @@ def test_traffic_record_only_while_sources_match(tmp_path, monkeypatch):
         f.write("\n")
     assert bench.ncu_traffic("k_example") is None
     assert bench.ncu_traffic("no_such_kernel") is None
+
+
+def test_threaded_oracle_sample_evaluates_every_site(ora):
+    """The all-cores CPU baseline splits the sampled sites over host threads
+    that call the oracle's per-site routine concurrently: the pieces, put
+    together, are the single-thread result bit for bit, and the timed helper
+    runs."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import numpy as np
+
+    from paper_1502_04025_gb300 import inputs
+
+    W = dict(bench.CONFIGS[1])
+    U = inputs.gauge_field(W["L"], W["eps"], W["gauge_seed"])
+    b = bench.make_sources(W)
+    sites = np.arange(int(np.prod(W["L"])))
+    whole = ora.apply_D_sites(W["L"], U, W["csw"], W["kappa"], b, sites)
+    with ThreadPoolExecutor(4) as ex:
+        parts = list(ex.map(lambda c: ora.apply_D_sites(W["L"], U, W["csw"], W["kappa"], b, c),
+                            np.array_split(sites, 7)))
+    assert np.array_equal(np.concatenate(parts), whole)
+    assert bench.oracle_sample_threads(W, U, b, 512, 3) > 0
