@@ -107,8 +107,10 @@ def parse():
     ap.add_argument("--no-dslash", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true", help="skip the plain FP64 path on the same system")
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--dist-backend", choices=["nccl", "gloo"], default="nccl",
-                    help="torch.distributed backend of a multi-GPU run (gloo: exchanges through host tensors)")
+    ap.add_argument("--dist-backend", choices=["nccl", "gloo"], default="gloo",
+                    help=("torch.distributed backend of a multi-GPU run (gloo, the default: face slots and "
+                          "boundary planes exchanged through host tensors, the path run end to end; nccl: "
+                          "through CUDA tensors)"))
     ap.add_argument("--replicas", action="store_true",
                     help="with several GPUs, solve one copy of the workload per GPU instead of sharding it")
     return ap.parse_args()
