@@ -164,14 +164,8 @@ struct Field {
 // vector access), quad q of all the domain's sites before quad q+1 (offset
 // (k/4)*4*Vd + 4s + k%4).  A 16-bit field's per-site scale is indexed by site.
 // (Quad planes took the FP16 operator on 32^3x64 from 173.0 to 165.7 us; the
-// BF16 operator measured 177.7 against 180.3 us in planes, so it keeps them.)
-template <typename S>
-__host__ __device__ __forceinline__ int64_t sp_off(int k, int s, int Vd)
-{
-    if constexpr (S::kQuad) return (int64_t)(k >> 2) * 4 * Vd + (int64_t)s * 4 + (k & 3);
-    else return (int64_t)k * Vd + s;
-}
-
+// BF16 operator measured 177.7 us in planes and 180.3 us in quads, so it keeps
+// planes.)
 __device__ __forceinline__ float2 word_f2(uint32_t w, const __half2 *)
 {
     __half2 h;

@@ -180,12 +180,6 @@ __host__ __device__ constexpr size_t sap_smem_layout(int Vd, bool stl, bool stc)
 // The paired-thread form uses pair planes (32^3x64 FP32: 0.682 -> 0.651 ms
 // per half-sweep); the one-thread form measured slower with them (48^3x96
 // BF16: 2.300 -> 2.343 ms) and keeps planes.
-template <bool PP, typename R>
-__device__ __forceinline__ int hf_idx(int k, int s, int Vh)
-{
-    return (PP && sizeof(R) == 4) ? ((k >> 1) * Vh + s) * 2 + (k & 1) : k * Vh + s;
-}
-
 template <int N, bool PP, typename R>
 __device__ __forceinline__ void hf_load(const cpx<R> *f, int k0, int s, int Vh, cpx<R> *x)
 {
