@@ -217,7 +217,9 @@ __device__ __forceinline__ void hf_store(cpx<R> *f, int k0, int s, int Vh, const
 // the compiler schedules across hops (48^3x96 BF16: 2.298 -> 2.283 ms per
 // half-sweep, the same bits).  The t hops keep their branches: a warp of
 // sites on a t face of the domain skips one of them whole (branch-free t
-// measured 2.316 ms).
+// measured 2.316 ms).  With 16-bit links only: the one-thread form with FP32
+// links (8x4^3 domains, 16^3x32) measured slower branch-free (50.1 against
+// 48.9 us per half-sweep).
 constexpr bool kBranchFreeHops = true;
 
 template <typename R, typename SL, typename SC, typename SS, typename SP, bool STL, bool STC, bool PP = false>
@@ -294,7 +296,7 @@ struct SapBlock {
     __device__ __forceinline__ void inner_dir_e(int s, uint16_t ef, uint16_t eb, const cpx<R> *src, int src_off,
                                                 cpx<R> *acc) const
     {
-        if constexpr (kBranchFreeHops && !PP && !SWAP && sizeof(R) == 4 && MU < 3) {
+        if constexpr (kBranchFreeHops && !PP && !SWAP && sizeof(R) == 4 && MU < 3 && !std::is_same<SL, StF32>::value) {
             // every lane evaluates both hops (a dropped one from slot 0 with
             // its own link) and adds them with weight 1 or 0
             const bool okf = !(ef & kCross) && QDD_IN_RANGE((ef & kSlotMask) - src_off, 0, Vh);
