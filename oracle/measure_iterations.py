@@ -2,9 +2,9 @@
 
 Runs the FP64 oracle's SAP-FGMRES(16) to a relative residual of 1e-10 on the
 16^3x32 workload (eps 0.5, c_sw 1.0, kappa 0.125, 8x4x4x4 domains, nmr 4,
-ncy 4, Gaussian source) and writes the counts to iterations_16c32.json.  The
-benchmark's CPU baseline times a bounded sample of oracle iterations and
-scales it by this count to a time-to-solution.  Only oracle/ code runs here.
+ncy 4, Gaussian source) and writes the counts to iterations_16c32.json.  A
+GPU test holds the CUDA path's solve of the same workload to this iteration
+count (within one) and residual history.  Only oracle/ code runs here.
 """
 import json
 import os

@@ -137,3 +137,41 @@ def test_solve_residual_at_sampled_sites(big, ora):
     print(f"PARITY fullsize {big.name} solve iters {rep['iters']} reported {rep['true_rel_res']:.3e} "
           f"sampled |r_S|/|b| {worst_norm:.3e} worst site {worst_site:.3e}")
     assert worst_norm <= 1e-10 and worst_site <= 1e-10
+
+
+def test_solve_16c32_iterations_match_the_oracle():
+    """The 16^3x32 workload (FP32 Schwarz on 8x4^3 domains, FP64 outer) takes
+    the FP64 oracle's SAP-FGMRES iteration count within one (stored in
+    oracle/iterations_16c32.json by oracle/measure_iterations.py, which runs
+    only the oracle), and its true residual meets the tolerance."""
+    import json
+    import os
+
+    from paper_1502_04025_gb300 import build, inputs
+
+    build.build()
+    from paper_1502_04025_gb300 import qdd
+
+    with open(os.path.join(os.path.dirname(__file__), "..", "oracle", "iterations_16c32.json")) as f:
+        ref = json.load(f)
+    w = ref["workload"]
+    L, dom = tuple(w["L"]), tuple(w["dom"])
+    ctx = qdd.qdd_create(0, 0)
+    g = qdd.qdd_create_gauge_field(ctx, L, dom, inputs.gauge_field(L, w["eps"], w["gauge_seed"]))
+    try:
+        qdd.qdd_set_clover(g, w["csw"], w["kappa"])
+        b = inputs.gaussian_source(L, w["source_seed"])
+        x, rep = qdd.qdd_solve(g, b, tol=w["tol"], restart_m=w["m"], nmr=w["nmr"], ncy=w["ncy"], sap_prec="f32",
+                               arnoldi_prec="df64", relax_eta=1e-6)
+        print(f"16^3x32: {rep['iters']} iterations (oracle {ref['iterations']}), true residual "
+              f"{rep['true_rel_res']:.2e} (oracle {ref['true_rel_res']:.2e})")
+        assert rep["converged"] and rep["true_rel_res"] <= w["tol"]
+        assert abs(rep["iters"] - ref["iterations"]) <= 1
+        # the estimated residual history follows the oracle's, step by step, to the
+        # FP32 preconditioner's rounding
+        hist = rep["history"][: len(ref["history"]) - 1]
+        for k, (h, r) in enumerate(zip(hist, ref["history"])):
+            assert abs(h - r) <= 1e-3 * r + 1e-12, (k, h, r)
+    finally:
+        qdd.qdd_destroy_gauge(g)
+        qdd.qdd_destroy(ctx)
