@@ -106,3 +106,26 @@ def test_threaded_oracle_sample_evaluates_every_site(ora):
                             np.array_split(sites, 7)))
     assert np.array_equal(np.concatenate(parts), whole)
     assert bench.oracle_sample_threads(W, U, b, 512, 3) > 0
+
+
+def test_reference_arm_line(tmp_path):
+    """bench.py --impl reference (the FP64 oracle timed on the host) prints
+    one JSON line with the contract's keys: its measured value, a
+    cpu_baseline describing this run with the same value, and an e2e object
+    without host-device traffic."""
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--config", "1",
+                        "--steps", "2", "--warmup", "1"], cwd=root, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "ms"
+    assert d["value"] > 0 and d["ms_per_step"] == d["value"] and d["steps"] == 2 and d["warmup"] == 1
+    assert d["higher_is_better"] is False
+    c = d["cpu_baseline"]
+    assert c["kind"] == "oracle" and c["cores"] == 1 and c["value"] == d["value"] and c["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
